@@ -63,14 +63,24 @@ static double det_d(int d, const double A[3][3])
          + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
 }
 
-/* Levi-Civita symbol for indices in {0,1,2}. */
-static int eps3(int i, int j, int k)
+/* 2 x 2 minor of A without row i and column j (3 x 3 A). */
+static double minor3(const double A[3][3], int i, int j)
 {
-    if (i == j || j == k || i == k) return 0;
-    return ((i == 0 && j == 1) || (i == 1 && j == 2) || (i == 2 && j == 0)) ? 1 : -1;
+    int r0 = i == 0 ? 1 : 0, r1 = i == 2 ? 1 : 2;
+    int c0 = j == 0 ? 1 : 0, c1 = j == 2 ? 1 : 2;
+    return A[r0][c0] * A[r1][c1] - A[r0][c1] * A[r1][c0];
 }
 
-/* Cofactor matrix cof(A), so that d det(A) / dA = cof(A) and A^-T = cof(A)/det A. */
+/* Directional derivative of minor3 along dA (product rule on the 2 x 2 det). */
+static double dminor3(const double A[3][3], const double dA[3][3], int i, int j)
+{
+    int r0 = i == 0 ? 1 : 0, r1 = i == 2 ? 1 : 2;
+    int c0 = j == 0 ? 1 : 0, c1 = j == 2 ? 1 : 2;
+    return dA[r0][c0] * A[r1][c1] + A[r0][c0] * dA[r1][c1] - dA[r0][c1] * A[r1][c0] - A[r0][c1] * dA[r1][c0];
+}
+
+/* Cofactor matrix cof(A)_ij = (-1)^(i+j) M_ij (signed minors), so that
+ * d det(A) / dA = cof(A) and A^-T = cof(A)/det A. */
 static void cof_d(int d, const double A[3][3], double C[3][3])
 {
     memset(C, 0, sizeof(double) * 9);
@@ -80,15 +90,7 @@ static void cof_d(int d, const double A[3][3], double C[3][3])
         return;
     }
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m)
-                for (int n = 0; n < 3; ++n)
-                    for (int p = 0; p < 3; ++p)
-                        for (int q = 0; q < 3; ++q)
-                            s += 0.5 * eps3(i, m, n) * eps3(j, p, q) * A[m][p] * A[n][q];
-            C[i][j] = s;
-        }
+        for (int j = 0; j < 3; ++j) C[i][j] = ((i + j) % 2 ? -1.0 : 1.0) * minor3(A, i, j);
 }
 
 /* Directional derivative of cof(A) along dA. */
@@ -101,15 +103,7 @@ static void dcof_d(int d, const double A[3][3], const double dA[3][3], double dC
         return;
     }
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m)
-                for (int n = 0; n < 3; ++n)
-                    for (int p = 0; p < 3; ++p)
-                        for (int q = 0; q < 3; ++q)
-                            s += eps3(i, m, n) * eps3(j, p, q) * A[m][p] * dA[n][q];
-            dC[i][j] = s;
-        }
+        for (int j = 0; j < 3; ++j) dC[i][j] = ((i + j) % 2 ? -1.0 : 1.0) * dminor3(A, dA, i, j);
 }
 
 static void inv_d(int d, const double A[3][3], double Ai[3][3])
