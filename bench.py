@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the simulator's hot path on GB300.
+
+One step = one pass of the whole hot path on the large 3D workload: a
+Newton-CG quasistatic solve from the rest shape (FP32 HVP inside FP64
+Newton control), the loss gradient, the adjoint CG solve and the parameter
+VJP.  The workload is a 4 x 2 x 2 box as a 128 x 64 x 64 hex grid, 6 tets per
+hex (3,145,728 tets, 545,025 vertices), jittered, neo-Hookean + muscle,
+min-y face pinned, gravity on; seeded synthetic inputs.
+
+Printed JSON line (rank 0):
+  value      element-HVPs per second over whole steps (n_elem x CG iterations
+             of the forward and adjoint solves, divided by the step time);
+  e2e        the same through the public API with host buffers, including the
+             host<->device copies of every step's inputs and outputs;
+  roofline   the HVP tile kernel: algorithmic bytes per launch (72 B per tet +
+             36 B per vertex) / its mean duration, against the HBM peak;
+  cpu_baseline  the FP64 checker timed on a bounded sample of the same solve.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank solves its own copy of the workload (no
+collective on the data path), value = all ranks' element-HVPs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_TET = 72.0     # conn 16 + Dm^-1 36 + W 4 + fiber 12 + a 4 (FP32 3D HVP)
+BYTES_PER_VERT = 36.0    # read x 12 + read v 12 + write Hv 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c5", "c3", "c5_eighth"], default="c5")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    import synth
+    if name == "c5":
+        return synth.make_config5(), "box 4x2x2, 128x64x64 hex x 6 tets (3,145,728 tets, 545,025 vertices), quasistatic Newton-CG + adjoint + VJP"
+    if name == "c5_eighth":
+        return synth.make_config5(2), "box 4x2x2, 64x32x32 hex x 6 tets (393,216 tets), quasistatic Newton-CG + adjoint + VJP"
+    return synth.make_config3(), "box 2x1x1, 32x16x16 hex x 5 tets (40,960 tets), quasistatic Newton-CG + adjoint + VJP"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    src = os.path.join(ROOT, "paper_2102_05791_gb300", "csrc", "elem_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(workload_name):
+    """DRAM bytes per launch of the HVP tile kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "hvp_tile_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        if d.get("elem_kernels_sha") == kernel_source_hash() and d.get("workload") == workload_name:
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- reference arm / CPU baseline
+
+def oracle_sample(p, max_cg):
+    """The FP64 checker on a bounded sample of the same solve: the first Newton
+    step of the quasistatic solve with its CG capped at max_cg iterations."""
+    import oracle
+    m = oracle.make_model(p)
+    t0 = time.perf_counter()
+    x, st = m.newton(p.a, rtol=1e-8, max_newton=1, max_cg=max_cg)
+    dt = time.perf_counter() - t0
+    hvps = st["cg_iters_total"]
+    return p.n_elem * hvps / dt, dt, hvps
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p, desc = workload(args.workload)
+    max_cg = 3 if args.workload == "c5" else 20
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, hvps = oracle_sample(p, max_cg)
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.median(v for v, _ in vals)
+    ms = 1000.0 * statistics.median(dt for _, dt in vals)
+    sample = (f"first Newton step of the {args.workload} solve with CG capped at {max_cg} iterations "
+              f"({p.n_elem} tets), FP64 checker, single thread")
+    line = {"impl": "reference", "metric": "element-HVP/s (fwd Newton-CG + adjoint, whole step)", "value": value,
+            "unit": "elem-HVP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": "elem-HVP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "elem-HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2102_05791_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p, desc = workload(args.workload)
+    sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle, density=p.density,
+                        gravity=p.gravity, precision=args.precision, device=dev)
+    a = torch.from_numpy(p.a).to(dev)
+    tgt = torch.from_numpy(p.target).to(dev)
+    n = p.n_vert
+
+    def loss_grad(x):
+        return ((x.mean(dim=0) - tgt) / n).expand(n, p.dim).contiguous()
+
+    def step(x_init=None, a_in=None):
+        x, st = sim.solve(a if a_in is None else a_in, x_init=x_init)
+        lam, sta = sim.adjoint(x, a if a_in is None else a_in, loss_grad(x))
+        g = sim.param_vjp(x, lam)
+        return x, g, st["cg_iters_total"] + sta["cg_iters_total"], st, sta
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    hvps = 0
+    launches0 = sim.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        x, g, h, st, sta = step()
+        hvps += h
+        last = (st, sta)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sim.kernel_launches() - launches0
+    # end-to-end through the public API with host buffers
+    X_host = torch.from_numpy(p.X).pin_memory()
+    a_host = torch.from_numpy(p.a).pin_memory()
+    out_g = torch.empty(p.n_elem, dtype=torch.float64).pin_memory()
+    out_x = torch.empty((n, p.dim), dtype=torch.float64).pin_memory()
+    e2e_hvps = 0
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        xi = X_host.to(dev, non_blocking=True)
+        ai = a_host.to(dev, non_blocking=True)
+        x, g, h, _, _ = step(x_init=xi, a_in=ai)
+        out_g.copy_(g, non_blocking=True)
+        out_x.copy_(x, non_blocking=True)
+        e2e_hvps += h
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = f0.elapsed_time(f1)
+    # HVP tile kernel timing on the converged state (same stream, CUDA events)
+    tile_ms, fin_ms = sim.time_hvp(50)
+
+    vals = torch.tensor([ms, ms_e2e, float(hvps), float(e2e_hvps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        t = vals[:2].clone()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = vals[2:].clone()
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        vals = torch.cat([t, c])
+    ms, ms_e2e, hvps_all, e2e_all = [float(v) for v in vals.cpu()]
+    if rank != 0:
+        return
+    value = p.n_elem * hvps_all / (ms / 1000.0)
+    e2e_value = p.n_elem * e2e_all / (ms_e2e / 1000.0)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = BYTES_PER_TET * p.n_elem + BYTES_PER_VERT * p.n_vert
+    achieved = alg_bytes / (tile_ms / 1000.0) / 1e9
+    line = {
+        "metric": "element-HVP/s (fwd Newton-CG + adjoint, whole step)",
+        "value": value,
+        "unit": "elem-HVP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 HVP/CG vectors, f64 state+gradient+energy+reductions" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision,
+                   "l2": f"inputs larger than L2: {(BYTES_PER_TET * p.n_elem) / 1e6:.0f} MB element data per HVP"},
+        "solves_per_s": world * args.steps / (ms / 1000.0),
+        "hvp_per_step": hvps_all / args.steps / world,
+        "newton_iters": last[0]["newton_iters"],
+        "cg_iters_fwd": last[0]["cg_iters_total"],
+        "cg_iters_adj": last[1]["cg_iters_total"],
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": "elem-HVP/s",
+                "h2d_bytes_per_step": int(X_host.numel() * 8 + a_host.numel() * 8),
+                "d2h_bytes_per_step": int(out_g.numel() * 8 + out_x.numel() * 8)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                     "kernel": "k_tile_hvp<float,3>", "kernel_ms": tile_ms, "finalize_ms": fin_ms,
+                     "peak_source": peak_kind},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        max_cg = 8 if args.workload == "c5" else 40
+        v, dt, nh = oracle_sample(p, max_cg)
+        line["cpu_baseline"] = {"value": v, "unit": "elem-HVP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first Newton step of the same solve, CG capped at {max_cg} iterations "
+                                          f"({nh} HVPs, {dt:.1f} s), FP64 checker, single thread"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

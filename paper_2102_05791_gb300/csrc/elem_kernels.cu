@@ -1,0 +1,827 @@
+// Element kernels: energy, gradient, Hessian-vector product and parameter
+// VJP of the neo-Hookean + muscle energy on triangle (D = 2) and tet (D = 3)
+// meshes.
+//
+// Model (Sec. 2, Eq. neohookean-psi; 3D form with I1 - 3):
+//   F = Ds Dm^-1 = I + Du Dm^-1 (Du: edge matrix of the displacement u = x - X,
+//   which keeps F accurate in FP32), J = det F,
+//   Psi = mu/2 (|F|^2 - D) - mu l(J) + lambda/2 l(J)^2,
+//   l = log (exact) or q(J) = (J-1) - (J-1)^2/2 (quadratic stand-in),
+//   muscle Psi_m = k/2 a |F f|^2.
+// Writing P_el = mu F + c(J) cof(F) with c = (lambda l - mu) l', the
+// differential is dP = mu dF + c'(J) (cof F : dF) cof F + c(J) dcof(F)[dF].
+// The element force matrix is G = W dPsi/dF Dm^-T; column j goes to vertex
+// j+1 and minus the column sum to vertex 0 (f = -grad E, Eq. f-as-grad; the
+// HVP is the paper's Eq. matrix-free-dfdx written out analytically).
+//
+// Each CTA processes one tile: it stages the tile's vertex values in shared
+// memory, evaluates its elements (one thread per element, coalesced SoA
+// loads), writes the per-corner results to shared memory, and then one
+// thread per tile vertex adds that vertex's corners in a fixed order.
+// Vertices shared with other tiles go through halo slots and a finalize
+// kernel, so every sum has one fixed order: no float atomics.
+#include <cstdio>
+
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace softsim {
+
+// ---------------------------------------------------------------- element math
+
+__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ double dlog(double x) { return log(x); }
+
+template <int D>
+struct FI {
+    static constexpr int B = 0;               // Dm^-1, D*D fields row-major
+    static constexpr int G = D * D;           // g = Dm^-1 f, D fields
+    static constexpr int W = D * D + D;       // rest measure
+    static constexpr int F = D * D + D + 1;   // fiber f, D fields
+    static constexpr int N = D * D + 2 * D + 1;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void cof(const T F[D][D], T C[D][D])
+{
+    if constexpr (D == 2) {
+        C[0][0] = F[1][1];
+        C[0][1] = -F[1][0];
+        C[1][0] = -F[0][1];
+        C[1][1] = F[0][0];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int a = (j + 1) % 3, b = (j + 2) % 3;  // column j = F[:,a] x F[:,b]
+            C[0][j] = F[1][a] * F[2][b] - F[2][a] * F[1][b];
+            C[1][j] = F[2][a] * F[0][b] - F[0][a] * F[2][b];
+            C[2][j] = F[0][a] * F[1][b] - F[1][a] * F[0][b];
+        }
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void dcof(const T F[D][D], const T dF[D][D], T C[D][D])
+{
+    if constexpr (D == 2) {
+        C[0][0] = dF[1][1];
+        C[0][1] = -dF[1][0];
+        C[1][0] = -dF[0][1];
+        C[1][1] = dF[0][0];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int a = (j + 1) % 3, b = (j + 2) % 3;
+            C[0][j] = dF[1][a] * F[2][b] - dF[2][a] * F[1][b] + F[1][a] * dF[2][b] - F[2][a] * dF[1][b];
+            C[1][j] = dF[2][a] * F[0][b] - dF[0][a] * F[2][b] + F[2][a] * dF[0][b] - F[0][a] * dF[2][b];
+            C[2][j] = dF[0][a] * F[1][b] - dF[1][a] * F[0][b] + F[0][a] * dF[1][b] - F[1][a] * dF[0][b];
+        }
+    }
+}
+
+// l(J), c(J) and c'(J) for P_el = mu F + c(J) cof(F).
+template <typename T>
+__device__ __forceinline__ void log_terms(int mode, T mu, T lam, T J, T &l, T &c, T &cp)
+{
+    if (mode == 0) {
+        const T iJ = T(1) / J;
+        l = dlog(J);
+        c = (lam * l - mu) * iJ;
+        cp = (lam + mu - lam * l) * iJ * iJ;
+    } else {
+        const T jm = J - T(1);
+        const T q = jm - T(0.5) * jm * jm;
+        const T qp = T(1) - jm;
+        l = q;
+        c = (lam * q - mu) * qp;
+        cp = lam * qp * qp - (lam * q - mu);
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void load_B(const ElemDev<T> &ed, int64_t e, T B[D][D])
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) B[i][j] = __ldg(ed.field(FI<D>::B + i * D + j) + e);
+}
+
+// Edge matrix (columns k = vertex k+1 minus vertex 0) of a staged vertex field.
+template <typename T, int D>
+__device__ __forceinline__ void edges(const T *s, const int lid[D + 1], T E[D][D])
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const T v0 = s[lid[0] * D + i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) E[i][k] = s[lid[k + 1] * D + i] - v0;
+    }
+}
+
+// M = A B (D x D), plus the identity when add_eye.
+template <typename T, int D>
+__device__ __forceinline__ void mul(const T A[D][D], const T B[D][D], T M[D][D], bool add_eye)
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T s = (add_eye && i == j) ? T(1) : T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += A[i][k] * B[k][j];
+            M[i][j] = s;
+        }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T detF(const T F[D][D], const T C[D][D])
+{
+    T J = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) J += F[i][0] * C[i][0];
+    return J;
+}
+
+template <int D>
+__device__ __forceinline__ void unpack(uint32_t cw, int lid[D + 1])
+{
+#pragma unroll
+    for (int k = 0; k <= D; ++k) lid[k] = (cw >> (8 * k)) & 0xffu;
+}
+
+// Write G's columns to the corner buffer (corner-major: conflict-free stores).
+template <typename T, int D>
+__device__ __forceinline__ void store_corners(T *scr, int max_te, int le, const T G[D][D])
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            scr[((j + 1) * D + i) * max_te + le] = G[i][j];
+            s += G[i][j];
+        }
+        scr[(0 * D + i) * max_te + le] = -s;
+    }
+}
+
+// Sum of the corners touching local vertex k (fixed increasing order).
+template <typename T, int D>
+__device__ __forceinline__ void gather_corners(const TileDev &td, const T *scr, int vs, int k, T acc[D])
+{
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = T(0);
+    const int s0 = td.inc_start[vs + k], s1 = td.inc_start[vs + k + 1];
+    for (int s = s0; s < s1; ++s) {
+        const int cid = td.inc[s];
+        const int le = cid / (D + 1), corner = cid - le * (D + 1);
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] += scr[(corner * D + c) * td.max_te + le];
+    }
+}
+
+// Per-vertex potential terms: gravity m g y and ground penalty kc max(0,-y)^p.
+__device__ __forceinline__ double pen_pow(double pen, int p) { return p == 2 ? pen * pen : pen * pen * pen; }
+
+// ---------------------------------------------------------------- energy
+
+// One launch evaluates the energy at u + t_j dir for n_trials step lengths,
+// sharing the element loads; FP64 throughout.
+template <int D>
+__global__ void __launch_bounds__(256) k_tile_energy(TileDev td, ElemDev<double> ed, VertDev vd, Phys ph,
+                                                     const double *__restrict__ u, const double *__restrict__ dir,
+                                                     const double *__restrict__ uhat, const double *__restrict__ a,
+                                                     TrialT tr, double *__restrict__ partials,
+                                                     DevScalars *__restrict__ sc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *su = reinterpret_cast<double *>(smem);
+    double *sd = su + td.max_tv * D;
+    const int t = blockIdx.x;
+    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
+    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    const int nt = tr.n;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int64_t gid = td.lv_gid[vs + k];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            su[k * D + c] = u[gid * D + c];
+            sd[k * D + c] = dir ? dir[gid * D + c] : 0.0;
+        }
+    }
+    __syncthreads();
+    double Eacc[kMaxTrials], Sacc[kMaxTrials];
+#pragma unroll
+    for (int j = 0; j < kMaxTrials; ++j) Eacc[j] = Sacc[j] = 0.0;
+    double minJ = INFINITY;
+    const double mu = ph.mu, lam = ph.lam;
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
+        const int64_t e = es + le;
+        int lid[D + 1];
+        unpack<D>(td.conn[e], lid);
+        double B[D][D], Du[D][D], Dd[D][D], Z0[D][D], Zd[D][D];
+        load_B<double, D>(ed, e, B);
+        edges<double, D>(su, lid, Du);
+        edges<double, D>(sd, lid, Dd);
+        mul<double, D>(Du, B, Z0, true);
+        mul<double, D>(Dd, B, Zd, false);
+        const double W = __ldg(ed.field(FI<D>::W) + e);
+        double f[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) f[i] = __ldg(ed.field(FI<D>::F + i) + e);
+        const double ka = ph.k * a[e];
+#pragma unroll
+        for (int j = 0; j < kMaxTrials; ++j) {
+            if (j >= nt) break;
+            const double tj = tr.t[j];
+            double F[D][D], C[D][D];
+#pragma unroll
+            for (int r = 0; r < D; ++r)
+#pragma unroll
+                for (int q = 0; q < D; ++q) F[r][q] = Z0[r][q] + tj * Zd[r][q];
+            cof<double, D>(F, C);
+            const double J = detF<double, D>(F, C);
+            if (j == 0) minJ = fmin(minJ, J);
+            double I1 = 0.0, Ff2 = 0.0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                double ff = 0.0;
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    I1 += F[r][q] * F[r][q];
+                    ff += F[r][q] * f[q];
+                }
+                Ff2 += ff * ff;
+            }
+            double l;
+            if (ph.log_mode == 0) {
+                l = J > 0.0 ? log(J) : 0.0;
+            } else {
+                const double jm = J - 1.0;
+                l = jm - 0.5 * jm * jm;
+            }
+            double w = ph.s_el * W * (0.5 * mu * (I1 - D) - mu * l + 0.5 * lam * l * l + 0.5 * ka * Ff2);
+            if (ph.log_mode == 0 && !(J > 0.0)) w = INFINITY;
+            Eacc[j] += w;
+            Sacc[j] += fabs(w);
+        }
+    }
+    // per-vertex terms, added by each vertex's owner tile
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int code = td.lv_code[vs + k];
+        if (code >= 0 && !(code & 1)) continue;
+        const int64_t gid = td.lv_gid[vs + k];
+        const double m = vd.mass[gid];
+        const double X1 = vd.X[gid * D + 1];
+#pragma unroll
+        for (int j = 0; j < kMaxTrials; ++j) {
+            if (j >= nt) break;
+            const double tj = tr.t[j];
+            const double y = X1 + su[k * D + 1] + tj * sd[k * D + 1];
+            const double pen = y < 0.0 ? -y : 0.0;
+            double w = ph.s_el * (m * ph.grav * y + ph.kc * pen_pow(pen, ph.cpow));
+            double s = fabs(w);
+            if (ph.dyn) {
+                double in = 0.0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    const double r = su[k * D + c] + tj * sd[k * D + c] - uhat[gid * D + c];
+                    in += 0.5 * m * r * r;
+                }
+                w += in;
+                s += in;
+            }
+            Eacc[j] += w;
+            Sacc[j] += s;
+        }
+    }
+    const int nb = gridDim.x;
+    for (int j = 0; j < nt; ++j) {
+        double e = block_sum(Eacc[j]);
+        double s = block_sum(Sacc[j]);
+        if (threadIdx.x == 0) {
+            partials[(size_t)j * nb + t] = e;
+            partials[(size_t)(kMaxTrials + j) * nb + t] = s;
+        }
+    }
+    double mj = block_min(minJ);
+    if (threadIdx.x == 0) partials[(size_t)(2 * kMaxTrials) * nb + t] = mj;
+    if (last_block(&sc->ticket[TK_ENERGY], nb)) {
+        for (int j = 0; j < nt; ++j) {
+            double e = sum_partials(partials + (size_t)j * nb, nb);
+            double s = sum_partials(partials + (size_t)(kMaxTrials + j) * nb, nb);
+            if (threadIdx.x == 0) {
+                sc->E[j] = e;
+                sc->S[j] = s;
+            }
+        }
+        double m = min_partials(partials + (size_t)(2 * kMaxTrials) * nb, nb);
+        if (threadIdx.x == 0) sc->minJ = m;
+    }
+}
+
+// ---------------------------------------------------------------- gradient
+
+template <int D>
+__global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> ed, VertDev vd, Phys ph,
+                                                   const double *__restrict__ u, const double *__restrict__ uhat,
+                                                   const double *__restrict__ a, double *__restrict__ g,
+                                                   double *__restrict__ hp, double *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *su = reinterpret_cast<double *>(smem);
+    double *scr = su + td.max_tv * D;
+    const int t = blockIdx.x;
+    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
+    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int64_t gid = td.lv_gid[vs + k];
+#pragma unroll
+        for (int c = 0; c < D; ++c) su[k * D + c] = u[gid * D + c];
+    }
+    __syncthreads();
+    const double mu = ph.mu, lam = ph.lam;
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
+        const int64_t e = es + le;
+        int lid[D + 1];
+        unpack<D>(td.conn[e], lid);
+        double B[D][D], Du[D][D], F[D][D], C[D][D];
+        load_B<double, D>(ed, e, B);
+        edges<double, D>(su, lid, Du);
+        mul<double, D>(Du, B, F, true);
+        cof<double, D>(F, C);
+        const double J = detF<double, D>(F, C);
+        double l, cc, cp;
+        log_terms<double>(ph.log_mode, mu, lam, J, l, cc, cp);
+        const double W = __ldg(ed.field(FI<D>::W) + e) * ph.s_el;
+        double f[D], gv[D], Ff[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            f[i] = __ldg(ed.field(FI<D>::F + i) + e);
+            gv[i] = __ldg(ed.field(FI<D>::G + i) + e);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < D; ++q) s += F[i][q] * f[q];
+            Ff[i] = s;
+        }
+        const double ka = ph.k * a[e];
+        double G[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += (mu * F[i][k] + cc * C[i][k]) * B[j][k];
+                G[i][j] = W * (s + ka * Ff[i] * gv[j]);
+            }
+        store_corners<double, D>(scr, td.max_te, le, G);
+    }
+    __syncthreads();
+    double gn2 = 0.0;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        double acc[D];
+        gather_corners<double, D>(td, scr, vs, k, acc);
+        const int code = td.lv_code[vs + k];
+        const int64_t gid = td.lv_gid[vs + k];
+        if (code < 0) {
+            const double m = vd.mass[gid];
+            const double y = vd.X[gid * D + 1] + su[k * D + 1];
+            const double pen = y < 0.0 ? -y : 0.0;
+            const double dcon = pen > 0.0 ? -ph.cpow * ph.kc * (ph.cpow == 2 ? pen : pen * pen) : 0.0;
+            acc[1] += ph.s_el * (m * ph.grav + dcon);
+            if (ph.dyn)
+#pragma unroll
+                for (int c = 0; c < D; ++c) acc[c] += m * (su[k * D + c] - uhat[gid * D + c]);
+            const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const double o = fx ? 0.0 : acc[c];
+                g[gid * D + c] = o;
+                gn2 += o * o;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
+        }
+    }
+    const double s = block_sum(gn2);
+    if (threadIdx.x == 0) partials[t] = s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys ph, const double *__restrict__ u,
+                                                  const double *__restrict__ uhat, const double *__restrict__ hp,
+                                                  double *__restrict__ g, double *__restrict__ partials,
+                                                  DevScalars *__restrict__ sc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double gn2 = 0.0;
+    if (i < td.n_fin) {
+        const int64_t gid = td.fin_gid[i];
+        double acc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = 0.0;
+        for (int s = td.fin_ptr[i]; s < td.fin_ptr[i + 1]; ++s)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += hp[(int64_t)s * D + c];
+        const double m = vd.mass[gid];
+        const double y = vd.X[gid * D + 1] + u[gid * D + 1];
+        const double pen = y < 0.0 ? -y : 0.0;
+        const double dcon = pen > 0.0 ? -ph.cpow * ph.kc * (ph.cpow == 2 ? pen : pen * pen) : 0.0;
+        acc[1] += ph.s_el * (m * ph.grav + dcon);
+        if (ph.dyn)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += m * (u[gid * D + c] - uhat[gid * D + c]);
+        const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double o = fx ? 0.0 : acc[c];
+            g[gid * D + c] = o;
+            gn2 += o * o;
+        }
+    }
+    const double s = block_sum(gn2);
+    const int base = td.n_tiles;
+    if (threadIdx.x == 0) partials[base + blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_GRAD], gridDim.x)) {
+        const double tot = sum_partials(partials, base + gridDim.x);
+        if (threadIdx.x == 0) sc->gn2 = tot;
+    }
+}
+
+// ---------------------------------------------------------------- HVP
+
+template <typename T, int D, bool CG>
+__global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
+                                                  const T *__restrict__ u, const T *__restrict__ a,
+                                                  const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
+                                                  double *__restrict__ partials, const DevScalars *__restrict__ sc)
+{
+    if (CG && sc->done) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *su = reinterpret_cast<T *>(smem);
+    T *sv = su + td.max_tv * D;
+    T *scr = sv + td.max_tv * D;
+    const int t = blockIdx.x;
+    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
+    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int64_t gid = td.lv_gid[vs + k];
+        const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            su[k * D + c] = u[gid * D + c];
+            sv[k * D + c] = fx ? T(0) : v[gid * D + c];
+        }
+    }
+    __syncthreads();
+    const T mu = T(ph.mu), lam = T(ph.lam);
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
+        const int64_t e = es + le;
+        int lid[D + 1];
+        unpack<D>(td.conn[e], lid);
+        T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D];
+        load_B<T, D>(ed, e, B);
+        T gv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) gv[i] = __ldg(ed.field(FI<D>::G + i) + e);
+        const T W = __ldg(ed.field(FI<D>::W) + e) * T(ph.s_el);
+        const T ka = T(ph.k) * a[e];
+        edges<T, D>(su, lid, Du);
+        edges<T, D>(sv, lid, Dv);
+        mul<T, D>(Du, B, F, true);
+        mul<T, D>(Dv, B, dF, false);
+        cof<T, D>(F, C);
+        dcof<T, D>(F, dF, dC);
+        const T J = detF<T, D>(F, C);
+        T dJ = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) dJ += C[i][j] * dF[i][j];
+        T l, cc, cp;
+        log_terms<T>(ph.log_mode, mu, lam, J, l, cc, cp);
+        const T cpdJ = cp * dJ;
+        T dvg[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
+            dvg[i] = ka * s;
+        }
+        T G[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                T s = T(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
+                G[i][j] = W * (s + dvg[i] * gv[j]);
+            }
+        store_corners<T, D>(scr, td.max_te, le, G);
+    }
+    __syncthreads();
+    double dot = 0.0;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        T acc[D];
+        gather_corners<T, D>(td, scr, vs, k, acc);
+        const int code = td.lv_code[vs + k];
+        const int64_t gid = td.lv_gid[vs + k];
+        if (code < 0) {
+            if (ph.kc > 0.0) {
+                const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
+                const double pen = yy < 0.0 ? -yy : 0.0;
+                const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+                acc[1] += T(ph.s_el * d2) * sv[k * D + 1];
+            }
+            if (ph.dyn) {
+                const T m = T(vd.mass[gid]);
+#pragma unroll
+                for (int c = 0; c < D; ++c) acc[c] += m * sv[k * D + c];
+            }
+            const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const T o = fx ? T(0) : acc[c];
+                y[gid * D + c] = o;
+                if (CG) dot += (double)sv[k * D + c] * (double)o;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
+        }
+    }
+    if (CG) {
+        const double s = block_sum(dot);
+        if (threadIdx.x == 0) partials[t] = s;
+    }
+}
+
+template <typename T, int D, bool CG>
+__global__ void __launch_bounds__(256) k_fin_hvp(TileDev td, VertDev vd, Phys ph, const T *__restrict__ u,
+                                                 const T *__restrict__ v, const T *__restrict__ hp, T *__restrict__ y,
+                                                 double *__restrict__ partials, DevScalars *__restrict__ sc)
+{
+    if (CG && sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dot = 0.0;
+    if (i < td.n_fin) {
+        const int64_t gid = td.fin_gid[i];
+        const bool fx = vd.fixed[gid] != 0;
+        T acc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = T(0);
+        for (int s = td.fin_ptr[i]; s < td.fin_ptr[i + 1]; ++s)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += hp[(int64_t)s * D + c];
+        T vv[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) vv[c] = fx ? T(0) : v[gid * D + c];
+        if (ph.kc > 0.0) {
+            const double yy = vd.X[gid * D + 1] + (double)u[gid * D + 1];
+            const double pen = yy < 0.0 ? -yy : 0.0;
+            const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+            acc[1] += T(ph.s_el * d2) * vv[1];
+        }
+        if (ph.dyn) {
+            const T m = T(vd.mass[gid]);
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += m * vv[c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const T o = fx ? T(0) : acc[c];
+            y[gid * D + c] = o;
+            if (CG) dot += (double)vv[c] * (double)o;
+        }
+    }
+    if (CG) {
+        const double s = block_sum(dot);
+        const int base = td.n_tiles;
+        if (threadIdx.x == 0) partials[base + blockIdx.x] = s;
+        if (last_block(&sc->ticket[TK_FIN], gridDim.x)) {
+            const double pAp = sum_partials(partials, base + gridDim.x);
+            if (threadIdx.x == 0) {
+                sc->pAp = pAp;
+                if (pAp > 0.0 && isfinite(pAp)) {
+                    sc->alpha = sc->rr / pAp;
+                } else {
+                    sc->alpha = 0.0;
+                    sc->negcurv = 1;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- parameter VJP
+
+template <int D>
+__global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed, VertDev vd, Phys ph,
+                                                  const double *__restrict__ u, const double *__restrict__ lam,
+                                                  double *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *su = reinterpret_cast<double *>(smem);
+    double *sl = su + td.max_tv * D;
+    const int t = blockIdx.x;
+    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
+    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int64_t gid = td.lv_gid[vs + k];
+        const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            su[k * D + c] = u[gid * D + c];
+            sl[k * D + c] = fx ? 0.0 : lam[gid * D + c];
+        }
+    }
+    __syncthreads();
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
+        const int64_t e = es + le;
+        int lid[D + 1];
+        unpack<D>(td.conn[e], lid);
+        double B[D][D], Du[D][D], Dl[D][D], F[D][D];
+        load_B<double, D>(ed, e, B);
+        edges<double, D>(su, lid, Du);
+        edges<double, D>(sl, lid, Dl);
+        mul<double, D>(Du, B, F, true);
+        double f[D], gv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            f[i] = __ldg(ed.field(FI<D>::F + i) + e);
+            gv[i] = __ldg(ed.field(FI<D>::G + i) + e);
+        }
+        double dot = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double Ff = 0.0, dFf = 0.0;
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                Ff += F[i][q] * f[q];
+                dFf += Dl[i][q] * gv[q];  // dF(lam) f = Dlam Dm^-1 f = Dlam g
+            }
+            dot += Ff * dFf;
+        }
+        const double W = __ldg(ed.field(FI<D>::W) + e);
+        out[td.perm[e]] = -ph.s_el * W * ph.k * dot;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline size_t smem_verts(const Ctx &c, size_t elt, int nfields)
+{
+    return (size_t)c.td.max_tv * c.dim * nfields * elt;
+}
+
+void launch_energy(const Ctx &c, const Phys &ph, const double *u, const double *dir, const double *uhat,
+                   const double *a, const double *t, int n_trials, cudaStream_t s)
+{
+    c.n_launch += 1;
+    TrialT tr;
+    tr.n = n_trials;
+    for (int j = 0; j < kMaxTrials; ++j) tr.t[j] = j < n_trials ? t[j] : 0.0;
+    const size_t sm = smem_verts(c, sizeof(double), 2);
+    if (c.dim == 2)
+        k_tile_energy<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, dir, uhat, a, tr, c.partials, c.sc);
+    else
+        k_tile_energy<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, dir, uhat, a, tr, c.partials, c.sc);
+}
+
+void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uhat, const double *a, double *g,
+                 double *hp, cudaStream_t s)
+{
+    c.n_launch += 2;
+    const size_t sm = smem_verts(c, sizeof(double), 1) + (size_t)c.td.max_te * (c.dim + 1) * c.dim * sizeof(double);
+    const int fb = c.n_fin_blocks;
+    if (c.dim == 2) {
+        k_tile_grad<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, uhat, a, g, hp, c.partials);
+        k_fin_grad<2><<<fb, 256, 0, s>>>(c.td, c.vd, ph, u, uhat, hp, g, c.partials, c.sc);
+    } else {
+        k_tile_grad<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, uhat, a, g, hp, c.partials);
+        k_fin_grad<3><<<fb, 256, 0, s>>>(c.td, c.vd, ph, u, uhat, hp, g, c.partials, c.sc);
+    }
+}
+
+template <typename T>
+static const ElemDev<T> &edev(const Ctx &c);
+template <>
+const ElemDev<float> &edev<float>(const Ctx &c) { return c.e32; }
+template <>
+const ElemDev<double> &edev<double>(const Ctx &c) { return c.e64; }
+
+template <typename T>
+size_t hvp_smem(const Ctx &c)
+{
+    return smem_verts(c, sizeof(T), 2) + (size_t)c.td.max_te * (c.dim + 1) * c.dim * sizeof(T);
+}
+
+template <typename T, bool CG>
+static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const size_t sm = hvp_smem<T>(c);
+    if (c.dim == 2)
+        k_tile_hvp<T, 2, CG><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+    else
+        k_tile_hvp<T, 3, CG><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+}
+
+template <typename T, bool CG>
+static void hvp_fin(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, const T *hp, cudaStream_t s)
+{
+    c.n_launch += 1;
+    if (c.dim == 2)
+        k_fin_hvp<T, 2, CG><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y, c.partials, c.sc);
+    else
+        k_fin_hvp<T, 3, CG><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y, c.partials, c.sc);
+}
+
+template <typename T>
+void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, bool with_dot,
+                cudaStream_t s)
+{
+    if (with_dot) {
+        hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
+        hvp_fin<T, true>(c, ph, u, v, y, hp, s);
+    } else {
+        hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
+        hvp_fin<T, false>(c, ph, u, v, y, hp, s);
+    }
+}
+
+template <typename T>
+void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
+                          cudaStream_t s)
+{
+    hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
+}
+
+template <typename T>
+void launch_hvp_finalize_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, const T *hp,
+                              cudaStream_t s)
+{
+    hvp_fin<T, false>(c, ph, u, v, y, hp, s);
+}
+
+void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *lam, double *dLda,
+                      cudaStream_t s)
+{
+    c.n_launch += 1;
+    const size_t sm = smem_verts(c, sizeof(double), 2);
+    if (c.dim == 2)
+        k_tile_vjp<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, lam, dLda);
+    else
+        k_tile_vjp<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, lam, dLda);
+}
+
+// Opt every kernel that may need more than 48 KB of dynamic shared memory into
+// the larger carve-out.
+cudaError_t configure_elem_kernels()
+{
+    const int big = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+#define SET(k) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    SET((k_tile_energy<2>));
+    SET((k_tile_energy<3>));
+    SET((k_tile_grad<2>));
+    SET((k_tile_grad<3>));
+    SET((k_tile_hvp<float, 2, true>));
+    SET((k_tile_hvp<float, 3, true>));
+    SET((k_tile_hvp<float, 2, false>));
+    SET((k_tile_hvp<float, 3, false>));
+    SET((k_tile_hvp<double, 2, true>));
+    SET((k_tile_hvp<double, 3, true>));
+    SET((k_tile_hvp<double, 2, false>));
+    SET((k_tile_hvp<double, 3, false>));
+    SET((k_tile_vjp<2>));
+    SET((k_tile_vjp<3>));
+#undef SET
+    return e;
+}
+
+template void launch_hvp<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
+                                float *, bool, cudaStream_t);
+template void launch_hvp<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
+                                 double *, double *, bool, cudaStream_t);
+template void launch_hvp_tile_only<float>(const Ctx &, const Phys &, const float *, const float *, const float *,
+                                          float *, float *, cudaStream_t);
+template void launch_hvp_tile_only<double>(const Ctx &, const Phys &, const double *, const double *,
+                                           const double *, double *, double *, cudaStream_t);
+template void launch_hvp_finalize_only<float>(const Ctx &, const Phys &, const float *, const float *, float *,
+                                              const float *, cudaStream_t);
+template void launch_hvp_finalize_only<double>(const Ctx &, const Phys &, const double *, const double *,
+                                               double *, const double *, cudaStream_t);
+template size_t hvp_smem<float>(const Ctx &);
+template size_t hvp_smem<double>(const Ctx &);
+
+}  // namespace softsim

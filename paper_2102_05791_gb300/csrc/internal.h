@@ -1,0 +1,189 @@
+// Internal structures shared by the translation units of libsoftsim.
+//
+// Data layout in device memory (one handle = one mesh):
+//   * Elements are stored in "tile order": a locality-preserving (Morton)
+//     order cut into tiles of at most max_te elements touching at most
+//     max_tv (<= 256) vertices.  perm[e] maps tile order -> caller order.
+//   * Per-element static data is structure-of-arrays, one field per array of
+//     `stride` entries: Dm^-1 (dim*dim fields, row-major), g = Dm^-1 f (dim),
+//     W (1), f (dim).  The HVP reads only the first dim*dim + dim + 1 fields.
+//   * conn[e] packs the element's dim+1 tile-local vertex ids, 8 bits each.
+//   * A tile's local vertices are lv_gid[tile_vert[t] .. tile_vert[t+1]),
+//     sorted by global id.  lv_code < 0: the vertex belongs to this tile only
+//     and the tile writes its final value; otherwise the tile writes a partial
+//     sum to halo slot (lv_code >> 1) and bit 0 says whether this tile is the
+//     vertex's owner (first tile touching it; owners add per-vertex energy
+//     terms).  Halo and element-less vertices are listed in fin_gid; their
+//     partial-sum slots are fin_ptr[i] .. fin_ptr[i+1], in tile order, so
+//     every vertex sum is formed in one fixed order (deterministic, no float
+//     atomics).
+//   * inc[inc_start[lv] .. inc_start[lv+1]) lists, in increasing order, the
+//     corners (local_elem*(dim+1) + corner) that touch local vertex lv.
+//   * Vertex fields are row-major [n_vert][dim].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace softsim {
+
+constexpr int kMaxTileVerts = 256;   // local ids fit in 8 bits
+constexpr int kMaxTrials = 8;        // step lengths evaluated per energy launch
+
+struct TileDev {
+    int n_tiles = 0;
+    int max_te = 0, max_tv = 0;
+    int n_fin = 0;
+    const int32_t *tile_elem = nullptr;  // [n_tiles + 1]
+    const int32_t *tile_vert = nullptr;  // [n_tiles + 1]
+    const int32_t *lv_gid = nullptr;     // [n_lv]
+    const int32_t *lv_code = nullptr;    // [n_lv]
+    const int32_t *inc_start = nullptr;  // [n_lv + 1]
+    const uint16_t *inc = nullptr;       // [n_elem * (dim+1)]
+    const uint32_t *conn = nullptr;      // [n_elem]
+    const int32_t *perm = nullptr;       // [n_elem] tile order -> caller order
+    const int32_t *fin_gid = nullptr;    // [n_fin]
+    const int32_t *fin_ptr = nullptr;    // [n_fin + 1]
+};
+
+template <typename T>
+struct ElemDev {
+    const T *base = nullptr;  // SoA block
+    int64_t stride = 0;       // entries per field
+    __host__ __device__ const T *field(int k) const { return base + (int64_t)k * stride; }
+};
+
+struct VertDev {
+    int64_t nv = 0;
+    const double *X = nullptr;      // [nv][dim] rest positions
+    const double *mass = nullptr;   // [nv]
+    const uint8_t *fixed = nullptr; // [nv]
+};
+
+// Physical scalars of one evaluation.  s_el scales the potential-energy
+// terms (dt^2 for the backward-Euler incremental potential, else 1); dyn
+// adds the inertia term 1/2 |x - xhat|_M^2 and its derivatives.
+struct Phys {
+    double mu = 0, lam = 0, k = 0, grav = 0, kc = 0;
+    int cpow = 3;
+    int log_mode = 0;
+    int dyn = 0;
+    double s_el = 1.0;
+};
+
+// Scalars that the kernels exchange in device memory (no host round trip).
+struct DevScalars {
+    // conjugate gradients
+    double rr, tol2, pAp, alpha, beta;
+    int iter, max_iter, done, negcurv;
+    // Newton
+    double gn2;      // |g|^2 of the FP64 gradient
+    double gd;       // g . d
+    int dir_fix;     // 1: CG gave no descent direction, d := -g
+    int pad0;
+    // energies of the line-search trials: E, sum |terms|, min J
+    double E[kMaxTrials], S[kMaxTrials];
+    double minJ;
+    int inverted;
+    int pad1;
+    unsigned int ticket[8];  // last-block-done counters, reset by the last block
+};
+
+struct TrialT {
+    int n;
+    double t[kMaxTrials];
+};
+
+enum Ticket { TK_CG = 0, TK_CGINIT = 1, TK_FIN = 2, TK_ENERGY = 3, TK_GD = 4, TK_GRAD = 5, TK_MISC = 6 };
+
+// Everything a launcher needs about one mesh.
+struct Ctx {
+    int dim = 0;
+    int64_t nv = 0, ne = 0;
+    TileDev td;
+    VertDev vd;
+    ElemDev<double> e64;
+    ElemDev<float> e32;
+    int threads = 256;
+    double *partials = nullptr;  // [n_partials] FP64 block partial sums
+    int n_fin_blocks = 1;
+    DevScalars *sc = nullptr;
+    mutable int64_t n_launch = 0;  // kernels launched through this context
+};
+
+// ---------------------------------------------------------------- launchers
+// Element kernels (elem_kernels.cu).  All vertex fields are displacements
+// u = x - X or directions, [nv][dim]; `a` is in tile order.
+
+// Multi-trial energy: for j < n_trials, E_j = energy at u + t_j dir (dir may
+// be null with n_trials = 1, t = 0).  Writes sc->E[j], sc->S[j], sc->minJ.
+void launch_energy(const Ctx &c, const Phys &ph, const double *u, const double *dir,
+                   const double *uhat, const double *a, const double *t, int n_trials,
+                   cudaStream_t s);
+
+// FP64 gradient of the energy (with inertia when ph.dyn), masked; writes
+// sc->gn2 = |g|^2.  hp: halo scratch [n_slots][dim] double.
+void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uhat,
+                 const double *a, double *g, double *hp, cudaStream_t s);
+
+// HVP y = A v (A = H, or M + dt^2 H when ph.dyn), masked.  With with_dot,
+// the finalize kernel also forms p.Ap into sc->pAp and the CG step length
+// sc->alpha.  `done` (device int, may be null) skips the launch body when set.
+template <typename T>
+void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
+                bool with_dot, cudaStream_t s);
+template <typename T>
+void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y,
+                          T *hp, cudaStream_t s);
+template <typename T>
+void launch_hvp_finalize_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y,
+                              const T *hp, cudaStream_t s);
+
+template <typename T>
+size_t hvp_smem(const Ctx &c);
+cudaError_t configure_elem_kernels();
+
+// dLda[perm[e]] = -s_el W k (F f).(dF(lam) f)
+void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *lam,
+                      double *dLda, cudaStream_t s);
+
+// ---------------------------------------------------------------- vector kernels (vec_kernels.cu)
+template <typename T>
+void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p, double rtol,
+                    int max_iter, cudaStream_t s);
+template <typename T>
+void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStream_t s);
+template <typename T>
+void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s);
+template <typename T>
+void launch_dir_check(const Ctx &c, const double *g, T *d, cudaStream_t s);
+template <typename T>
+void launch_step_update(const Ctx &c, double *u, const T *d, double t, float *u32, cudaStream_t s);
+
+void launch_x_to_u(const Ctx &c, const double *x, double *u, float *u32, const uint8_t *fixed_pin,
+                   cudaStream_t s);
+void launch_u_to_x(const Ctx &c, const double *u, double *x, cudaStream_t s);
+void launch_uhat(const Ctx &c, const double *x0, const double *v0, double dt, double *uhat,
+                 cudaStream_t s);
+template <typename T>
+void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
+void launch_mask_copy(const Ctx &c, const double *in, double *out, cudaStream_t s);
+// step backward: xbar0 = M lam - vbar1/dt, vbar0 = dt M lam (masked)
+void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt,
+                             double *xbar0, double *vbar0, cudaStream_t s);
+// b = xbar1 + vbar1/dt
+void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out,
+                     cudaStream_t s);
+// v1 = (x1 - x0)/dt
+int vec_grid_size(int64_t n);
+// r = b - Ax, |r|^2 -> sc->gn2
+void launch_residual(const Ctx &c, const double *b, const double *Ax, double *r, cudaStream_t s);
+// x += d
+template <typename T>
+void launch_accumulate(const Ctx &c, double *x, const T *d, cudaStream_t s);
+void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, double *v1,
+                     cudaStream_t s);
+
+}  // namespace softsim

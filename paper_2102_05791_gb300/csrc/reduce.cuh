@@ -1,0 +1,92 @@
+// Deterministic FP64 block reductions and the last-block-done pattern.
+//
+// Every reduction writes one partial per block; the block that finishes
+// last (integer ticket, so the result does not depend on arrival order)
+// sums the partials in index order.  Sums therefore come out bit-identical
+// from run to run.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace softsim {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ double block_min(double v)
+{
+    __shared__ double red[32];
+    v = warp_min(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = INFINITY;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? red[lane] : INFINITY;
+        r = warp_min(r);
+    }
+    return r;
+}
+
+// Call after thread 0 has written this block's partial(s).  Returns true in
+// every thread of the block that arrives last; that block resets the ticket.
+__device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int n_blocks)
+{
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == n_blocks - 1);
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+    return is_last;
+}
+
+// Fixed-order sum of n partials (bypassing L1: they were written by other
+// blocks); valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double *p, int n)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(p + i);
+    return block_sum(s);
+}
+
+__device__ __forceinline__ double min_partials(const double *p, int n)
+{
+    double s = INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmin(s, __ldcg(p + i));
+    return block_min(s);
+}
+
+}  // namespace softsim

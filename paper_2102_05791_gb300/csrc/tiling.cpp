@@ -1,0 +1,177 @@
+// Tile construction for the deterministic element -> vertex reduction.
+#include "tiling.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace softsim {
+
+static uint64_t spread3(uint64_t x)
+{
+    x &= 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+static uint64_t spread2(uint64_t x)
+{
+    x &= 0xffffffffull;
+    x = (x | x << 16) & 0x0000ffff0000ffffull;
+    x = (x | x << 8) & 0x00ff00ff00ff00ffull;
+    x = (x | x << 4) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | x << 2) & 0x3333333333333333ull;
+    x = (x | x << 1) & 0x5555555555555555ull;
+    return x;
+}
+
+bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, int te_max, int tv_max,
+                 TileBuild &out, std::string &err)
+{
+    const int nc = dim + 1;
+    out = TileBuild();
+    out.dim = dim;
+    out.nv = nv;
+    out.ne = ne;
+    if (tv_max > 256) tv_max = 256;
+    if (te_max < 1) te_max = 1;
+    if (te_max * nc > 65535) te_max = 65535 / nc;
+
+    // --- Morton order of element centroids, quantised at the mean element size
+    std::vector<double> lo(dim, INFINITY), hi(dim, -INFINITY);
+    for (int64_t i = 0; i < nv; ++i)
+        for (int c = 0; c < dim; ++c) {
+            lo[c] = std::min(lo[c], X[i * dim + c]);
+            hi[c] = std::max(hi[c], X[i * dim + c]);
+        }
+    double vol = 1.0;
+    for (int c = 0; c < dim; ++c) vol *= std::max(hi[c] - lo[c], 1e-300);
+    double cell = std::pow(vol / std::max<int64_t>(ne, 1) * (dim == 2 ? 2.0 : 6.0), 1.0 / dim);
+    if (!(cell > 0.0) || !std::isfinite(cell)) cell = 1.0;
+    const uint64_t qmax = dim == 2 ? 0xffffffffull : 0x1fffffull;
+    std::vector<uint64_t> code(ne);
+    for (int64_t e = 0; e < ne; ++e) {
+        uint64_t q[3] = {0, 0, 0};
+        for (int c = 0; c < dim; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < nc; ++k) s += X[(int64_t)T[e * nc + k] * dim + c];
+            double v = std::floor((s / nc - lo[c]) / cell);
+            if (v < 0) v = 0;
+            q[c] = std::min<uint64_t>((uint64_t)v, qmax);
+        }
+        code[e] = dim == 2 ? (spread2(q[0]) | spread2(q[1]) << 1)
+                           : (spread3(q[0]) | spread3(q[1]) << 1 | spread3(q[2]) << 2);
+    }
+    out.perm.resize(ne);
+    std::iota(out.perm.begin(), out.perm.end(), 0);
+    std::stable_sort(out.perm.begin(), out.perm.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
+
+    // --- greedy cut into tiles
+    std::vector<int32_t> stamp(nv, -1);
+    out.tile_elem.push_back(0);
+    int cur = 0, cur_ne = 0, cur_nv = 0;
+    for (int64_t i = 0; i < ne; ++i) {
+        const int32_t *t = T + (int64_t)out.perm[i] * nc;
+        int fresh = 0;
+        for (int k = 0; k < nc; ++k)
+            if (stamp[t[k]] != cur) ++fresh;
+        if (cur_ne > 0 && (cur_ne + 1 > te_max || cur_nv + fresh > tv_max)) {
+            out.tile_elem.push_back((int32_t)i);
+            ++cur;
+            cur_ne = cur_nv = 0;
+            fresh = nc;
+        }
+        if (fresh > tv_max) {
+            err = "element has more vertices than a tile allows";
+            return false;
+        }
+        for (int k = 0; k < nc; ++k)
+            if (stamp[t[k]] != cur) {
+                stamp[t[k]] = cur;
+                ++cur_nv;
+            }
+        ++cur_ne;
+    }
+    if (ne > 0) out.tile_elem.push_back((int32_t)ne);
+    out.n_tiles = (int)out.tile_elem.size() - 1;
+
+    // --- local vertices, packed connectivity, incidence lists
+    std::vector<int32_t> loc(nv, -1), cnt(nv, 0), first_tile(nv, -1);
+    out.conn.resize(ne);
+    out.inc.resize((size_t)ne * nc);
+    out.tile_vert.push_back(0);
+    std::vector<int32_t> verts, bucket;
+    for (int ti = 0; ti < out.n_tiles; ++ti) {
+        const int es = out.tile_elem[ti], ee = out.tile_elem[ti + 1];
+        verts.clear();
+        for (int i = es; i < ee; ++i)
+            for (int k = 0; k < nc; ++k) verts.push_back(T[(int64_t)out.perm[i] * nc + k]);
+        std::sort(verts.begin(), verts.end());
+        verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+        const int nl = (int)verts.size();
+        out.max_te = std::max(out.max_te, ee - es);
+        out.max_tv = std::max(out.max_tv, nl);
+        for (int j = 0; j < nl; ++j) {
+            loc[verts[j]] = j;
+            cnt[verts[j]] += 1;
+            if (first_tile[verts[j]] < 0) first_tile[verts[j]] = ti;
+        }
+        bucket.assign(nl + 1, 0);
+        for (int i = es; i < ee; ++i) {
+            uint32_t w = 0;
+            for (int k = 0; k < nc; ++k) {
+                const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
+                w |= (uint32_t)l << (8 * k);
+                bucket[l + 1] += 1;
+            }
+            out.conn[i] = w;
+        }
+        for (int j = 0; j < nl; ++j) bucket[j + 1] += bucket[j];
+        const int64_t base = (int64_t)es * nc;
+        for (int j = 0; j < nl; ++j) out.inc_start.push_back((int32_t)(base + bucket[j]));
+        std::vector<int> fill(bucket.begin(), bucket.end() - 1);
+        for (int i = es; i < ee; ++i)
+            for (int k = 0; k < nc; ++k) {
+                const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
+                out.inc[base + fill[l]++] = (uint16_t)((i - es) * nc + k);
+            }
+        for (int j = 0; j < nl; ++j) out.lv_gid.push_back(verts[j]);
+        out.tile_vert.push_back((int32_t)out.lv_gid.size());
+    }
+    out.inc_start.push_back((int32_t)((int64_t)ne * nc));
+
+    // --- halo vertices and their partial-sum slots
+    std::vector<int32_t> fin_index(nv, -1);
+    out.fin_ptr.push_back(0);
+    for (int64_t v = 0; v < nv; ++v) {
+        if (cnt[v] == 0) {
+            err = "vertex " + std::to_string(v) + " belongs to no element";
+            return false;
+        }
+        if (cnt[v] >= 2) {
+            fin_index[v] = (int32_t)out.fin_gid.size();
+            out.fin_gid.push_back((int32_t)v);
+            out.fin_ptr.push_back(out.fin_ptr.back() + cnt[v]);
+        }
+    }
+    out.n_slots = out.fin_ptr.back();
+    std::vector<int32_t> next(out.fin_ptr.begin(), out.fin_ptr.end() - 1);
+    out.lv_code.resize(out.lv_gid.size());
+    for (int ti = 0; ti < out.n_tiles; ++ti)
+        for (int j = out.tile_vert[ti]; j < out.tile_vert[ti + 1]; ++j) {
+            const int32_t v = out.lv_gid[j];
+            if (cnt[v] == 1) {
+                out.lv_code[j] = -1;
+            } else {
+                const int32_t slot = next[fin_index[v]]++;
+                out.lv_code[j] = slot * 2 + (first_tile[v] == ti ? 1 : 0);
+            }
+        }
+    return true;
+}
+
+}  // namespace softsim

@@ -1,0 +1,376 @@
+// Vector kernels of the conjugate-gradient and Newton loops.
+//
+// CG (Sec. 3: the adjoint system is solved matrix-free by conjugate
+// gradients; the same CG gives the Newton direction) keeps its scalars in
+// device memory: the finalize kernel of the HVP forms p.Ap and alpha,
+// cg_update forms r.r and beta and raises `done`, so a whole block of
+// iterations runs without a host round trip and can be captured in a CUDA
+// graph.  Every dot product is accumulated in FP64 with fixed-order
+// reductions.  Vectors are float (mixed precision) or double.
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace softsim {
+
+static inline int vec_grid(int64_t n)
+{
+    int64_t g = (n + 1023) / 1024;
+    if (g < 1) g = 1;
+    if (g > 1216) g = 1216;  // 152 SMs x 8
+    return (int)g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__restrict__ b, double sign,
+                                                 T *__restrict__ d, T *__restrict__ r, T *__restrict__ p, double rtol,
+                                                 int max_iter, double *__restrict__ partials, DevScalars *sc)
+{
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T ri = T(sign * b[i]);
+        r[i] = ri;
+        p[i] = ri;
+        d[i] = T(0);
+        rr += (double)ri * (double)ri;
+    }
+    const double s = block_sum(rr);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_CGINIT], gridDim.x)) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            sc->rr = tot;
+            sc->tol2 = rtol * rtol * tot;
+            sc->iter = 0;
+            sc->max_iter = max_iter;
+            sc->negcurv = 0;
+            sc->alpha = sc->beta = sc->pAp = 0.0;
+            sc->done = (tot <= sc->tol2 || max_iter <= 0 || !isfinite(tot)) ? 1 : 0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(int64_t n, T *__restrict__ d, T *__restrict__ r,
+                                                   const T *__restrict__ p, const T *__restrict__ Ap,
+                                                   double *__restrict__ partials, DevScalars *sc)
+{
+    if (sc->done) return;
+    const bool neg = sc->negcurv != 0;
+    const bool first = sc->iter == 0;
+    const T alpha = T(sc->alpha);
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (neg) {
+            if (first) d[i] = p[i];  // no curvature information yet: use the first direction
+        } else {
+            d[i] += alpha * p[i];
+            const T ri = r[i] - alpha * Ap[i];
+            r[i] = ri;
+            rr += (double)ri * (double)ri;
+        }
+    }
+    const double s = block_sum(rr);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_CG], gridDim.x)) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            if (neg) {
+                sc->done = 1;
+            } else {
+                sc->beta = tot / sc->rr;
+                sc->rr = tot;
+                sc->iter += 1;
+                if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, const T *__restrict__ r,
+                                                const DevScalars *sc)
+{
+    if (sc->done) return;
+    const T beta = T(sc->beta);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + beta * p[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dir_check(int64_t n, const double *__restrict__ g, const T *__restrict__ d,
+                                                   double *__restrict__ partials, DevScalars *sc)
+{
+    double gd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        gd += g[i] * (double)d[i];
+    const double s = block_sum(gd);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_GD], gridDim.x)) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            if (tot < 0.0 && isfinite(tot)) {
+                sc->gd = tot;
+                sc->dir_fix = 0;
+            } else {
+                sc->gd = -sc->gn2;
+                sc->dir_fix = 1;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dir_fix(int64_t n, const double *__restrict__ g, T *__restrict__ d,
+                                                 const DevScalars *sc)
+{
+    if (!sc->dir_fix) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = T(-g[i]);
+}
+
+template <typename T>
+__global__ void k_step_update(int64_t n, double *__restrict__ u, const T *__restrict__ d, double t,
+                              float *__restrict__ u32)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ui = u[i] + t * (double)d[i];
+        u[i] = ui;
+        if (u32) u32[i] = (float)ui;
+    }
+}
+
+__global__ void k_x_to_u(int64_t nv, int dim, const double *__restrict__ x, const double *__restrict__ X,
+                         const uint8_t *__restrict__ fixed, double *__restrict__ u, float *__restrict__ u32)
+{
+    const int64_t n = nv * dim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ui = (fixed && fixed[i / dim]) ? 0.0 : x[i] - X[i];
+        u[i] = ui;
+        if (u32) u32[i] = (float)ui;
+    }
+}
+
+__global__ void k_u_to_x(int64_t n, const double *__restrict__ u, const double *__restrict__ X, double *__restrict__ x)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = X[i] + u[i];
+}
+
+__global__ void k_uhat(int64_t n, const double *__restrict__ x0, const double *__restrict__ v0, double dt,
+                       const double *__restrict__ X, double *__restrict__ uhat)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        uhat[i] = (x0[i] + dt * v0[i]) - X[i];
+}
+
+template <typename T>
+__global__ void k_gather_elem(int64_t ne, const int32_t *__restrict__ perm, const double *__restrict__ user,
+                              T *__restrict__ internal)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
+        internal[e] = T(user[perm[e]]);
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(int64_t n, const Tin *__restrict__ in, Tout *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = Tout(in[i]);
+}
+
+__global__ void k_mask_copy(int64_t nv, int dim, const uint8_t *__restrict__ fixed, const double *__restrict__ in,
+                            double *__restrict__ out)
+{
+    const int64_t n = nv * dim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fixed[i / dim] ? 0.0 : in[i];
+}
+
+__global__ void k_step_bwd_combine(int64_t nv, int dim, const uint8_t *__restrict__ fixed,
+                                   const double *__restrict__ mass, const double *__restrict__ lam,
+                                   const double *__restrict__ vbar1, double dt, double *__restrict__ xbar0,
+                                   double *__restrict__ vbar0)
+{
+    const int64_t n = nv * dim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / dim;
+        const double ml = mass[v] * lam[i];
+        const bool fx = fixed[v] != 0;
+        xbar0[i] = fx ? 0.0 : ml - vbar1[i] / dt;
+        vbar0[i] = fx ? 0.0 : dt * ml;
+    }
+}
+
+__global__ void k_axpy_out(int64_t n, const double *__restrict__ x, const double *__restrict__ y, double beta,
+                           double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] + beta * y[i];
+}
+
+__global__ void k_velocity(int64_t n, const double *__restrict__ x1, const double *__restrict__ x0, double dt,
+                           double *__restrict__ v1)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v1[i] = (x1[i] - x0[i]) / dt;
+}
+
+// r = b - Ax (FP64) and |r|^2 into sc->gn2 (used by the adjoint refinement).
+__global__ void __launch_bounds__(256) k_residual(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax,
+                                                  double *__restrict__ r, double *__restrict__ partials, DevScalars *sc)
+{
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - (Ax ? Ax[i] : 0.0);
+        r[i] = ri;
+        rr += ri * ri;
+    }
+    const double s = block_sum(rr);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_MISC], gridDim.x)) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) sc->gn2 = tot;
+    }
+}
+
+template <typename T>
+__global__ void k_accumulate(int64_t n, double *__restrict__ x, const T *__restrict__ d)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+// ---------------------------------------------------------------- launchers
+
+void launch_residual(const Ctx &c, const double *b, const double *Ax, double *r, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_residual<<<vec_grid(n), 256, 0, s>>>(n, b, Ax, r, c.partials, c.sc);
+}
+
+template <typename T>
+void launch_accumulate(const Ctx &c, double *x, const T *d, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_accumulate<T><<<vec_grid(n), 256, 0, s>>>(n, x, d);
+}
+
+template <typename T>
+void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p, double rtol, int max_iter,
+                    cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_cg_init<T><<<vec_grid(n), 256, 0, s>>>(n, b, sign, d, r, p, rtol, max_iter, c.partials, c.sc);
+}
+
+template <typename T>
+void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_cg_update<T><<<vec_grid(n), 256, 0, s>>>(n, d, r, p, Ap, c.partials, c.sc);
+}
+
+template <typename T>
+void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_cg_dir<T><<<vec_grid(n), 256, 0, s>>>(n, p, r, c.sc);
+}
+
+template <typename T>
+void launch_dir_check(const Ctx &c, const double *g, T *d, cudaStream_t s)
+{
+    c.n_launch += 2;
+    const int64_t n = c.nv * c.dim;
+    k_dir_check<T><<<vec_grid(n), 256, 0, s>>>(n, g, d, c.partials, c.sc);
+    k_dir_fix<T><<<vec_grid(n), 256, 0, s>>>(n, g, d, c.sc);
+}
+
+template <typename T>
+void launch_step_update(const Ctx &c, double *u, const T *d, double t, float *u32, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_step_update<T><<<vec_grid(n), 256, 0, s>>>(n, u, d, t, u32);
+}
+
+void launch_x_to_u(const Ctx &c, const double *x, double *u, float *u32, const uint8_t *fixed, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_x_to_u<<<vec_grid(c.nv * c.dim), 256, 0, s>>>(c.nv, c.dim, x, c.vd.X, fixed, u, u32);
+}
+
+void launch_u_to_x(const Ctx &c, const double *u, double *x, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_u_to_x<<<vec_grid(n), 256, 0, s>>>(n, u, c.vd.X, x);
+}
+
+void launch_uhat(const Ctx &c, const double *x0, const double *v0, double dt, double *uhat, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int64_t n = c.nv * c.dim;
+    k_uhat<<<vec_grid(n), 256, 0, s>>>(n, x0, v0, dt, c.vd.X, uhat);
+}
+
+template <typename T>
+void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_gather_elem<T><<<vec_grid(c.ne), 256, 0, s>>>(c.ne, c.td.perm, user, internal);
+}
+
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s)
+{
+    k_convert<Tin, Tout><<<vec_grid(n), 256, 0, s>>>(n, in, out);
+}
+
+void launch_mask_copy(const Ctx &c, const double *in, double *out, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_mask_copy<<<vec_grid(c.nv * c.dim), 256, 0, s>>>(c.nv, c.dim, c.vd.fixed, in, out);
+}
+
+void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt, double *xbar0,
+                             double *vbar0, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_step_bwd_combine<<<vec_grid(c.nv * c.dim), 256, 0, s>>>(c.nv, c.dim, c.vd.fixed, c.vd.mass, lam, vbar1, dt,
+                                                              xbar0, vbar0);
+}
+
+void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out, cudaStream_t s)
+{
+    k_axpy_out<<<vec_grid(n), 256, 0, s>>>(n, x, y, beta, out);
+}
+
+void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, double *v1, cudaStream_t s)
+{
+    k_velocity<<<vec_grid(n), 256, 0, s>>>(n, x1, x0, dt, v1);
+}
+
+int vec_grid_size(int64_t n) { return vec_grid(n); }
+
+#define INST(T)                                                                                                     \
+    template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, cudaStream_t); \
+    template void launch_cg_update<T>(const Ctx &, T *, T *, const T *, const T *, cudaStream_t);                   \
+    template void launch_cg_dir<T>(const Ctx &, T *, const T *, cudaStream_t);                                      \
+    template void launch_dir_check<T>(const Ctx &, const double *, T *, cudaStream_t);                              \
+    template void launch_step_update<T>(const Ctx &, double *, const T *, double, float *, cudaStream_t);           \
+    template void launch_gather_elem<T>(const Ctx &, const double *, T *, cudaStream_t);                            \
+    template void launch_accumulate<T>(const Ctx &, double *, const T *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template void launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
+template void launch_convert<double, double>(int64_t, const double *, double *, cudaStream_t);
+
+}  // namespace softsim
