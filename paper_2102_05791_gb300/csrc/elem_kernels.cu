@@ -24,6 +24,7 @@
 
 #include "internal.h"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace softsim {
 
@@ -166,18 +167,20 @@ __device__ __forceinline__ void store_corners(T *scr, int max_te, int le, const 
     }
 }
 
-// Sum of the corners touching local vertex k (fixed increasing order).
+// Sum of the corners touching a local vertex, in the fixed increasing order of
+// its incidence list (inc points at the tile's incidence block, w is the
+// vertex's packed lv_inc word; scr is the corner buffer).
 template <typename T, int D>
-__device__ __forceinline__ void gather_corners(const TileDev &td, const T *scr, int vs, int k, T acc[D])
+__device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, int max_te, T acc[D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = T(0);
-    const int s0 = td.inc_start[vs + k], s1 = td.inc_start[vs + k + 1];
-    for (int s = s0; s < s1; ++s) {
-        const int cid = td.inc[s];
+    const int s0 = (int)(w & 0xffffu), n = (int)(w >> 16);
+    for (int s = s0; s < s0 + n; ++s) {
+        const int cid = inc[s];
         const int le = cid / (D + 1), corner = cid - le * (D + 1);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] += scr[(corner * D + c) * td.max_te + le];
+        for (int c = 0; c < D; ++c) acc[c] += scr[(corner * D + c) * max_te + le];
     }
 }
 
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256) k_tile_energy(TileDev td, ElemDev<double>
     // per-vertex terms, added by each vertex's owner tile
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int code = td.lv_code[vs + k];
-        if (code >= 0 && !(code & 1)) continue;
+        if (code == LV_PAD || (code >= 0 && !(code & 1))) continue;  // padding, or not the owner
         const int64_t gid = td.lv_gid[vs + k];
         const double m = vd.mass[gid];
         const double X1 = vd.X[gid * D + 1];
@@ -383,12 +386,14 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
     }
     __syncthreads();
     double gn2 = 0.0;
+    const uint16_t *tinc = td.inc + (int64_t)es * (D + 1);
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
-        double acc[D];
-        gather_corners<double, D>(td, scr, vs, k, acc);
         const int code = td.lv_code[vs + k];
+        if (code == LV_PAD) continue;
+        double acc[D];
+        gather_corners<double, D>(tinc, td.lv_inc[vs + k], scr, td.max_te, acc);
         const int64_t gid = td.lv_gid[vs + k];
-        if (code < 0) {
+        if (code == LV_INTERIOR) {
             const double m = vd.mass[gid];
             const double y = vd.X[gid * D + 1] + su[k * D + 1];
             const double pen = y < 0.0 ? -y : 0.0;
@@ -456,22 +461,80 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
 
 // ---------------------------------------------------------------- HVP
 
+// Shared-memory plan of the HVP tile kernel (offsets in bytes, all 16-byte
+// aligned because max_te is a multiple of 8 and max_tv of 4).
+template <typename T, int D>
+struct HvpSmem {
+    static constexpr int NF = D * D + D + 1;  // Dm^-1, g, W
+    size_t e, conn, a, inc, gid, code, linc, u, v, total;
+    __host__ __device__ HvpSmem(int max_te, int max_tv)
+    {
+        e = 16;
+        conn = e + (size_t)NF * max_te * sizeof(T);
+        a = conn + (size_t)max_te * 4;
+        inc = a + (size_t)max_te * sizeof(T);
+        gid = inc + (size_t)max_te * (D + 1) * 2;
+        code = gid + (size_t)max_tv * 4;
+        linc = code + (size_t)max_tv * 4;
+        u = linc + (size_t)max_tv * 4;
+        v = u + (size_t)max_tv * D * sizeof(T);
+        total = v + (size_t)max_tv * D * sizeof(T);
+    }
+};
+
+// HVP of one tile per CTA.  Thread 0 pulls the tile's element fields,
+// connectivity, activations, incidence lists and local-vertex tables into
+// shared memory with bulk copies on one mbarrier; the tile's vertex values
+// are then gathered, each thread evaluates dP(dF) for its elements from
+// shared memory, the per-corner forces overwrite the element fields in place
+// (the corner array needs (D+1)*D <= NF columns per element), and one thread
+// per local vertex adds its corners in fixed order.
 template <typename T, int D, bool CG>
 __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
                                                   const T *__restrict__ u, const T *__restrict__ a,
                                                   const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
-                                                  double *__restrict__ partials, const DevScalars *__restrict__ sc)
+                                                  double *__restrict__ partials, DevScalars *__restrict__ sc)
 {
     if (CG && sc->done) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *su = reinterpret_cast<T *>(smem);
-    T *sv = su + td.max_tv * D;
-    T *scr = sv + td.max_tv * D;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const HvpSmem<T, D> L(td.max_te, td.max_tv);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *sE = reinterpret_cast<T *>(smem + L.e);
+    const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
+    const T *sA = reinterpret_cast<const T *>(smem + L.a);
+    const uint16_t *sInc = reinterpret_cast<const uint16_t *>(smem + L.inc);
+    const int32_t *sGid = reinterpret_cast<const int32_t *>(smem + L.gid);
+    const int32_t *sCode = reinterpret_cast<const int32_t *>(smem + L.code);
+    const uint32_t *sLinc = reinterpret_cast<const uint32_t *>(smem + L.linc);
+    T *su = reinterpret_cast<T *>(smem + L.u);
+    T *sv = reinterpret_cast<T *>(smem + L.v);
     const int t = blockIdx.x;
     const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
     const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    const int mte = td.max_te;
+    constexpr int NF = HvpSmem<T, D>::NF;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        const uint32_t be = (uint32_t)ne_t * sizeof(T);
+        const uint32_t total = NF * be + (uint32_t)ne_t * 4 + be + (uint32_t)ne_t * (D + 1) * 2 + 3u * nlv * 4;
+        mbar_arrive_expect_tx(bar, total);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) bulk_g2s(sE + (size_t)f * mte, ed.field(f) + es, be, bar);
+        bulk_g2s(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar);
+        bulk_g2s(smem + L.a, a + es, be, bar);
+        bulk_g2s(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar);
+        bulk_g2s(smem + L.gid, td.lv_gid + vs, (uint32_t)nlv * 4, bar);
+        bulk_g2s(smem + L.code, td.lv_code + vs, (uint32_t)nlv * 4, bar);
+        bulk_g2s(smem + L.linc, td.lv_inc + vs, (uint32_t)nlv * 4, bar);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(bar, 0)) {
+        if (threadIdx.x == 0) atomicOr(&sc->kerr, 1);
+        mbar_wait_bounded(bar, 0);  // give copies in flight a last chance before the CTA exits
+        return;
+    }
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
-        const int64_t gid = td.lv_gid[vs + k];
+        const int64_t gid = sGid[k];
         const bool fx = vd.fixed[gid] != 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -481,17 +544,19 @@ __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, Ver
     }
     __syncthreads();
     const T mu = T(ph.mu), lam = T(ph.lam);
+    const T sel = T(ph.s_el), kk = T(ph.k);
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
-        const int64_t e = es + le;
         int lid[D + 1];
-        unpack<D>(td.conn[e], lid);
-        T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D];
-        load_B<T, D>(ed, e, B);
-        T gv[D];
+        unpack<D>(sConn[le], lid);
+        T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D], gv[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) gv[i] = __ldg(ed.field(FI<D>::G + i) + e);
-        const T W = __ldg(ed.field(FI<D>::W) + e) * T(ph.s_el);
-        const T ka = T(ph.k) * a[e];
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) B[i][j] = sE[(FI<D>::B + i * D + j) * mte + le];
+#pragma unroll
+        for (int i = 0; i < D; ++i) gv[i] = sE[(FI<D>::G + i) * mte + le];
+        const T W = sE[FI<D>::W * mte + le] * sel;
+        const T ka = kk * sA[le];
         edges<T, D>(su, lid, Du);
         edges<T, D>(sv, lid, Dv);
         mul<T, D>(Du, B, F, true);
@@ -525,16 +590,17 @@ __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, Ver
                 for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
                 G[i][j] = W * (s + dvg[i] * gv[j]);
             }
-        store_corners<T, D>(scr, td.max_te, le, G);
+        store_corners<T, D>(sE, mte, le, G);  // overwrites this element's own columns only
     }
     __syncthreads();
     double dot = 0.0;
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int code = sCode[k];
+        if (code == LV_PAD) continue;
         T acc[D];
-        gather_corners<T, D>(td, scr, vs, k, acc);
-        const int code = td.lv_code[vs + k];
-        const int64_t gid = td.lv_gid[vs + k];
-        if (code < 0) {
+        gather_corners<T, D>(sInc, sLinc[k], sE, mte, acc);
+        const int64_t gid = sGid[k];
+        if (code == LV_INTERIOR) {
             if (ph.kc > 0.0) {
                 const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
                 const double pen = yy < 0.0 ? -yy : 0.0;
@@ -671,7 +737,8 @@ __global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed
             dot += Ff * dFf;
         }
         const double W = __ldg(ed.field(FI<D>::W) + e);
-        out[td.perm[e]] = -ph.s_el * W * ph.k * dot;
+        const int32_t pe = td.perm[e];
+        if (pe >= 0) out[pe] = -ph.s_el * W * ph.k * dot;
     }
 }
 
@@ -721,7 +788,7 @@ const ElemDev<double> &edev<double>(const Ctx &c) { return c.e64; }
 template <typename T>
 size_t hvp_smem(const Ctx &c)
 {
-    return smem_verts(c, sizeof(T), 2) + (size_t)c.td.max_te * (c.dim + 1) * c.dim * sizeof(T);
+    return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv).total : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv).total;
 }
 
 template <typename T, bool CG>

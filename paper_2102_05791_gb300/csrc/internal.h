@@ -17,13 +17,19 @@
 //     partial-sum slots are fin_ptr[i] .. fin_ptr[i+1], in tile order, so
 //     every vertex sum is formed in one fixed order (deterministic, no float
 //     atomics).
-//   * inc[inc_start[lv] .. inc_start[lv+1]) lists, in increasing order, the
-//     corners (local_elem*(dim+1) + corner) that touch local vertex lv.
+//   * inc[tile_elem[t]*(dim+1) + s], s in [first, first+count) of lv_inc[lv],
+//     lists in increasing order the corners (local_elem*(dim+1) + corner)
+//     that touch local vertex lv.
+//   * Per-tile ranges are padded to 16-byte multiples for bulk copies;
+//     padding elements have W = 0 and perm -1, padding local vertices have
+//     lv_code == LV_PAD and no incidences.
 //   * Vertex fields are row-major [n_vert][dim].
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "layout.h"
 
 namespace softsim {
 
@@ -38,10 +44,10 @@ struct TileDev {
     const int32_t *tile_vert = nullptr;  // [n_tiles + 1]
     const int32_t *lv_gid = nullptr;     // [n_lv]
     const int32_t *lv_code = nullptr;    // [n_lv]
-    const int32_t *inc_start = nullptr;  // [n_lv + 1]
-    const uint16_t *inc = nullptr;       // [n_elem * (dim+1)]
-    const uint32_t *conn = nullptr;      // [n_elem]
-    const int32_t *perm = nullptr;       // [n_elem] tile order -> caller order
+    const uint32_t *lv_inc = nullptr;    // [n_lv] first incidence (within the tile) | count << 16
+    const uint16_t *inc = nullptr;       // [ne_int * (dim+1)]
+    const uint32_t *conn = nullptr;      // [ne_int]
+    const int32_t *perm = nullptr;       // [ne_int] tile order -> caller order, -1 = padding
     const int32_t *fin_gid = nullptr;    // [n_fin]
     const int32_t *fin_ptr = nullptr;    // [n_fin + 1]
 };
@@ -85,7 +91,7 @@ struct DevScalars {
     double E[kMaxTrials], S[kMaxTrials];
     double minJ;
     int inverted;
-    int pad1;
+    int kerr;        // kernel-side error flags (1: bulk-copy wait timed out)
     unsigned int ticket[8];  // last-block-done counters, reset by the last block
 };
 
@@ -99,7 +105,7 @@ enum Ticket { TK_CG = 0, TK_CGINIT = 1, TK_FIN = 2, TK_ENERGY = 3, TK_GD = 4, TK
 // Everything a launcher needs about one mesh.
 struct Ctx {
     int dim = 0;
-    int64_t nv = 0, ne = 0;
+    int64_t nv = 0, ne = 0, ne_int = 0;
     TileDev td;
     VertDev vd;
     ElemDev<double> e64;

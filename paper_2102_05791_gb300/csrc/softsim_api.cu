@@ -163,7 +163,7 @@ extern "C" int sim_tile_stats(const sim_handle *h, int *n_tiles, double *ept, do
     const int nt = h->tb.n_tiles;
     if (n_tiles) *n_tiles = nt;
     if (ept) *ept = nt ? (double)h->ne / nt : 0.0;
-    if (vpt) *vpt = nt ? (double)h->tb.lv_gid.size() / nt : 0.0;
+    if (vpt) *vpt = nt ? (double)h->tb.n_real_lv / nt : 0.0;
     if (halo) *halo = h->nv ? (double)h->tb.fin_gid.size() / h->nv : 0.0;
     return SIM_OK;
 }
@@ -212,7 +212,6 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     for (int64_t i = 0; i < nv * d; ++i)
         if (!std::isfinite(mesh->rest_pos[i])) return fail(h, SIM_ENAN, "non-finite rest position");
     const int nf = d * d + 2 * d + 1;
-    std::vector<double> edata((size_t)nf * ne);
     std::vector<double> mass(nv, 0.0);
     std::vector<double> Wv(ne);
     for (int64_t e = 0; e < ne; ++e) {
@@ -254,10 +253,13 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, te, kMaxTileVerts, h->tb, terr))
         return fail(h, SIM_EINVAL, "tiling: " + terr);
     const TileBuild &tb = h->tb;
+    const int64_t ne_int = tb.ne_int;
 
-    // element SoA in tile order
-    for (int64_t i = 0; i < ne; ++i) {
+    // element SoA in (padded) tile order; padding elements stay all-zero (W = 0)
+    std::vector<double> edata((size_t)nf * ne_int, 0.0);
+    for (int64_t i = 0; i < ne_int; ++i) {
         const int64_t e = tb.perm[i];
+        if (e < 0) continue;
         const int32_t *t = mesh->elems + e * nc;
         double Dm[3][3] = {{0}}, B[3][3] = {{0}};
         for (int k = 0; k < d; ++k)
@@ -285,14 +287,14 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
         if (mat->fiber)
             for (int c = 0; c < d; ++c) f[c] = mat->fiber[e * d + c];
         for (int r = 0; r < d; ++r)
-            for (int c = 0; c < d; ++c) edata[(size_t)(r * d + c) * ne + i] = B[r][c];
+            for (int c = 0; c < d; ++c) edata[(size_t)(r * d + c) * ne_int + i] = B[r][c];
         for (int r = 0; r < d; ++r) {
             double s = 0.0;
             for (int c = 0; c < d; ++c) s += B[r][c] * f[c];
-            edata[(size_t)(d * d + r) * ne + i] = s;
-            edata[(size_t)(d * d + d + 1 + r) * ne + i] = f[r];
+            edata[(size_t)(d * d + r) * ne_int + i] = s;
+            edata[(size_t)(d * d + d + 1 + r) * ne_int + i] = f[r];
         }
-        edata[(size_t)(d * d + d) * ne + i] = Wv[e];
+        edata[(size_t)(d * d + d) * ne_int + i] = Wv[e];
     }
 
     // --- upload
@@ -312,14 +314,15 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     c.dim = d;
     c.nv = nv;
     c.ne = ne;
+    c.ne_int = ne_int;
     c.e64.base = ce64;
-    c.e64.stride = ne;
+    c.e64.stride = ne_int;
     if (is_mixed(h)) {
         std::vector<float> e32(edata.begin(), edata.end());
         const float *ce32;
         if ((rc = upload(h, e32, &ce32))) return rc;
         c.e32.base = ce32;
-        c.e32.stride = ne;
+        c.e32.stride = ne_int;
     }
     c.vd.nv = nv;
     c.vd.X = h->X;
@@ -334,7 +337,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if ((rc = upload(h, tb.tile_vert, &td.tile_vert))) return rc;
     if ((rc = upload(h, tb.lv_gid, &td.lv_gid))) return rc;
     if ((rc = upload(h, tb.lv_code, &td.lv_code))) return rc;
-    if ((rc = upload(h, tb.inc_start, &td.inc_start))) return rc;
+    if ((rc = upload(h, tb.lv_inc, &td.lv_inc))) return rc;
     if ((rc = upload(h, tb.inc, &td.inc))) return rc;
     if ((rc = upload(h, tb.conn, &td.conn))) return rc;
     if ((rc = upload(h, tb.perm, &td.perm))) return rc;
@@ -346,7 +349,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
 
     // --- work buffers
     const int64_t nd = nv * d;
-    const int n_part = std::max({td.n_tiles + c.n_fin_blocks, vec_grid_size(nd), vec_grid_size(ne), 1});
+    const int n_part = std::max({td.n_tiles + c.n_fin_blocks, vec_grid_size(nd), vec_grid_size(ne_int), 1});
     c.partials = (double *)dalloc(h, sizeof(double) * (size_t)n_part * (2 * kMaxTrials + 1));
     h->sc = (DevScalars *)dalloc(h, sizeof(DevScalars));
     c.sc = h->sc;
@@ -360,14 +363,14 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     h->r64 = (double *)dalloc(h, sizeof(double) * nd);
     h->Hx = (double *)dalloc(h, sizeof(double) * nd);
     h->hp64 = (double *)dalloc(h, sizeof(double) * std::max<int64_t>(tb.n_slots, 1) * d);
-    h->a64 = (double *)dalloc(h, sizeof(double) * ne);
+    h->a64 = (double *)dalloc(h, sizeof(double) * ne_int);
     h->vd = dalloc(h, vbytes * nd);
     h->vr = dalloc(h, vbytes * nd);
     h->vp = dalloc(h, vbytes * nd);
     h->vAp = dalloc(h, vbytes * nd);
     if (is_mixed(h)) {
         h->u32 = (float *)dalloc(h, sizeof(float) * nd);
-        h->a32 = (float *)dalloc(h, sizeof(float) * ne);
+        h->a32 = (float *)dalloc(h, sizeof(float) * ne_int);
         h->hp32 = (float *)dalloc(h, sizeof(float) * std::max<int64_t>(tb.n_slots, 1) * d);
     }
     if (!c.partials || !h->sc || !h->u || !h->uhat || !h->g || !h->work || !h->lam || !h->lacc || !h->r64 || !h->Hx || !h->hp64 || !h->a64 || !h->vd ||

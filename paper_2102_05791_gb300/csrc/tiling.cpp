@@ -99,29 +99,41 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     if (ne > 0) out.tile_elem.push_back((int32_t)ne);
     out.n_tiles = (int)out.tile_elem.size() - 1;
 
-    // --- local vertices, packed connectivity, incidence lists
+    // --- padded layout: local vertices, packed connectivity, incidence lists
+    auto round_up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+    std::vector<int32_t> cut = out.tile_elem;  // unpadded cut points in Morton order
+    std::vector<int32_t> order = out.perm;
+    out.tile_elem.assign(1, 0);
+    for (int ti = 0; ti < out.n_tiles; ++ti)
+        out.tile_elem.push_back((int32_t)round_up(out.tile_elem.back() + (cut[ti + 1] - cut[ti]), kElemPad));
+    out.ne_int = out.tile_elem.back();
+    out.perm.assign(out.ne_int, -1);
+    for (int ti = 0; ti < out.n_tiles; ++ti)
+        for (int i = cut[ti]; i < cut[ti + 1]; ++i) out.perm[out.tile_elem[ti] + (i - cut[ti])] = order[i];
     std::vector<int32_t> loc(nv, -1), cnt(nv, 0), first_tile(nv, -1);
-    out.conn.resize(ne);
-    out.inc.resize((size_t)ne * nc);
+    out.conn.assign(out.ne_int, 0u);
+    out.inc.assign((size_t)out.ne_int * nc, 0);
     out.tile_vert.push_back(0);
     std::vector<int32_t> verts, bucket;
     for (int ti = 0; ti < out.n_tiles; ++ti) {
-        const int es = out.tile_elem[ti], ee = out.tile_elem[ti + 1];
+        const int es = out.tile_elem[ti];
+        const int n_real = cut[ti + 1] - cut[ti];
         verts.clear();
-        for (int i = es; i < ee; ++i)
+        for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) verts.push_back(T[(int64_t)out.perm[i] * nc + k]);
         std::sort(verts.begin(), verts.end());
         verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
         const int nl = (int)verts.size();
-        out.max_te = std::max(out.max_te, ee - es);
-        out.max_tv = std::max(out.max_tv, nl);
+        const int nl_pad = (int)round_up(nl, kVertPad);
+        out.max_te = std::max(out.max_te, out.tile_elem[ti + 1] - es);
+        out.max_tv = std::max(out.max_tv, nl_pad);
         for (int j = 0; j < nl; ++j) {
             loc[verts[j]] = j;
             cnt[verts[j]] += 1;
             if (first_tile[verts[j]] < 0) first_tile[verts[j]] = ti;
         }
         bucket.assign(nl + 1, 0);
-        for (int i = es; i < ee; ++i) {
+        for (int i = es; i < es + n_real; ++i) {
             uint32_t w = 0;
             for (int k = 0; k < nc; ++k) {
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
@@ -132,17 +144,22 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         }
         for (int j = 0; j < nl; ++j) bucket[j + 1] += bucket[j];
         const int64_t base = (int64_t)es * nc;
-        for (int j = 0; j < nl; ++j) out.inc_start.push_back((int32_t)(base + bucket[j]));
+        for (int j = 0; j < nl; ++j)
+            out.lv_inc.push_back((uint32_t)bucket[j] | ((uint32_t)(bucket[j + 1] - bucket[j]) << 16));
         std::vector<int> fill(bucket.begin(), bucket.end() - 1);
-        for (int i = es; i < ee; ++i)
+        for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) {
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
                 out.inc[base + fill[l]++] = (uint16_t)((i - es) * nc + k);
             }
         for (int j = 0; j < nl; ++j) out.lv_gid.push_back(verts[j]);
+        for (int j = nl; j < nl_pad; ++j) {
+            out.lv_gid.push_back(verts[0]);  // a valid id, never written
+            out.lv_inc.push_back(0u);
+        }
+        out.n_real_lv += nl;
         out.tile_vert.push_back((int32_t)out.lv_gid.size());
     }
-    out.inc_start.push_back((int32_t)((int64_t)ne * nc));
 
     // --- halo vertices and their partial-sum slots
     std::vector<int32_t> fin_index(nv, -1);
@@ -160,12 +177,13 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     }
     out.n_slots = out.fin_ptr.back();
     std::vector<int32_t> next(out.fin_ptr.begin(), out.fin_ptr.end() - 1);
-    out.lv_code.resize(out.lv_gid.size());
+    out.lv_code.assign(out.lv_gid.size(), LV_PAD);
     for (int ti = 0; ti < out.n_tiles; ++ti)
         for (int j = out.tile_vert[ti]; j < out.tile_vert[ti + 1]; ++j) {
+            if ((out.lv_inc[j] >> 16) == 0) continue;  // padding entry
             const int32_t v = out.lv_gid[j];
             if (cnt[v] == 1) {
-                out.lv_code[j] = -1;
+                out.lv_code[j] = LV_INTERIOR;
             } else {
                 const int32_t slot = next[fin_index[v]]++;
                 out.lv_code[j] = slot * 2 + (first_tile[v] == ti ? 1 : 0);

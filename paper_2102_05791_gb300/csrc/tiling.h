@@ -6,19 +6,30 @@
 #include <string>
 #include <vector>
 
+#include "layout.h"
+
 namespace softsim {
+
+// Padding makes every per-tile range start and end on a 16-byte boundary so
+// that it can be copied with one bulk (TMA) copy: element ranges are padded
+// to multiples of kElemPad entries (padding elements have W = 0, zero
+// connectivity and perm = -1) and local-vertex ranges to multiples of
+// kVertPad (padding entries have lv_code = LV_PAD and no incidences).
 
 struct TileBuild {
     int dim = 0;
     int64_t nv = 0, ne = 0;
-    int n_tiles = 0, max_te = 0, max_tv = 0;
+    int64_t ne_int = 0;              // padded element count (tile order)
+    int n_tiles = 0, max_te = 0, max_tv = 0;   // padded per-tile maxima
     int64_t n_slots = 0;
-    std::vector<int32_t> perm;       // tile order -> caller order
-    std::vector<int32_t> tile_elem;  // [n_tiles + 1]
-    std::vector<int32_t> tile_vert;  // [n_tiles + 1]
-    std::vector<int32_t> lv_gid, lv_code, inc_start;
-    std::vector<uint16_t> inc;
-    std::vector<uint32_t> conn;
+    int64_t n_real_lv = 0;           // local vertices without padding
+    std::vector<int32_t> perm;       // [ne_int] tile order -> caller order, -1 for padding
+    std::vector<int32_t> tile_elem;  // [n_tiles + 1] padded element offsets
+    std::vector<int32_t> tile_vert;  // [n_tiles + 1] padded local-vertex offsets
+    std::vector<int32_t> lv_gid, lv_code;
+    std::vector<uint32_t> lv_inc;    // (first incidence within the tile) | (count << 16)
+    std::vector<uint16_t> inc;       // [ne_int * (dim+1)]
+    std::vector<uint32_t> conn;      // [ne_int]
     std::vector<int32_t> fin_gid, fin_ptr;
 };
 

@@ -164,11 +164,13 @@ __global__ void k_uhat(int64_t n, const double *__restrict__ x0, const double *_
 }
 
 template <typename T>
-__global__ void k_gather_elem(int64_t ne, const int32_t *__restrict__ perm, const double *__restrict__ user,
+__global__ void k_gather_elem(int64_t ne_int, const int32_t *__restrict__ perm, const double *__restrict__ user,
                               T *__restrict__ internal)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
-        internal[e] = T(user[perm[e]]);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne_int; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t pe = perm[e];
+        internal[e] = pe >= 0 ? T(user[pe]) : T(0);
+    }
 }
 
 template <typename Tin, typename Tout>
@@ -323,7 +325,7 @@ template <typename T>
 void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s)
 {
     c.n_launch += 1;
-    k_gather_elem<T><<<vec_grid(c.ne), 256, 0, s>>>(c.ne, c.td.perm, user, internal);
+    k_gather_elem<T><<<vec_grid(c.ne_int), 256, 0, s>>>(c.ne_int, c.td.perm, user, internal);
 }
 
 template <typename Tin, typename Tout>
