@@ -30,8 +30,12 @@ namespace softsim {
 
 // ---------------------------------------------------------------- element math
 
-__device__ __forceinline__ float dlog(float x) { return logf(x); }
+// FP32 uses the hardware approximations (absolute log error < 2^-21 on
+// [0.5, 2]; it enters the HVP at the 1e-6 relative level); FP64 is exact.
+__device__ __forceinline__ float dlog(float x) { return __logf(x); }
 __device__ __forceinline__ double dlog(double x) { return log(x); }
+__device__ __forceinline__ float drcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double drcp(double x) { return 1.0 / x; }
 
 template <int D>
 struct FI {
@@ -85,7 +89,7 @@ template <typename T>
 __device__ __forceinline__ void log_terms(int mode, T mu, T lam, T J, T &l, T &c, T &cp)
 {
     if (mode == 0) {
-        const T iJ = T(1) / J;
+        const T iJ = drcp(J);
         l = dlog(J);
         c = (lam * l - mu) * iJ;
         cp = (lam + mu - lam * l) * iJ * iJ;
@@ -167,20 +171,19 @@ __device__ __forceinline__ void store_corners(T *scr, int max_te, int le, const 
     }
 }
 
-// Sum of the corners touching a local vertex, in the fixed increasing order of
-// its incidence list (inc points at the tile's incidence block, w is the
-// vertex's packed lv_inc word; scr is the corner buffer).
+// Sum of the corners touching a local vertex, in the fixed order of its
+// incidence list (inc points at the tile's incidence block, each entry the
+// corner's offset in the corner buffer; w is the vertex's lv_inc word).
 template <typename T, int D>
 __device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, int max_te, T acc[D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = T(0);
-    const int s0 = (int)(w & 0xffffu), n = (int)(w >> 16);
+    const int s0 = (int)(w & 0xffffu), n = (int)((w >> 16) & kLvCountMask);
     for (int s = s0; s < s0 + n; ++s) {
-        const int cid = inc[s];
-        const int le = cid / (D + 1), corner = cid - le * (D + 1);
+        const T *p = scr + inc[s];
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] += scr[(corner * D + c) * max_te + le];
+        for (int c = 0; c < D; ++c) acc[c] += p[c * max_te];
     }
 }
 
@@ -469,7 +472,7 @@ struct HvpSmem {
     size_t e, conn, a, inc, gid, code, linc, u, v, total;
     __host__ __device__ HvpSmem(int max_te, int max_tv)
     {
-        e = 16;
+        e = 16;  // two mbarriers
         conn = e + (size_t)NF * max_te * sizeof(T);
         a = conn + (size_t)max_te * 4;
         inc = a + (size_t)max_te * sizeof(T);
@@ -489,8 +492,8 @@ struct HvpSmem {
 // shared memory, the per-corner forces overwrite the element fields in place
 // (the corner array needs (D+1)*D <= NF columns per element), and one thread
 // per local vertex adds its corners in fixed order.
-template <typename T, int D, bool CG>
-__global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
+template <typename T, int D, bool CG, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
                                                   const T *__restrict__ u, const T *__restrict__ a,
                                                   const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
                                                   double *__restrict__ partials, DevScalars *__restrict__ sc)
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, Ver
     if (CG && sc->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const HvpSmem<T, D> L(td.max_te, td.max_tv);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
     T *sE = reinterpret_cast<T *>(smem + L.e);
     const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
     const T *sA = reinterpret_cast<const T *>(smem + L.a);
@@ -515,34 +518,46 @@ __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, Ver
     constexpr int NF = HvpSmem<T, D>::NF;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
-        const uint32_t be = (uint32_t)ne_t * sizeof(T);
-        const uint32_t total = NF * be + (uint32_t)ne_t * 4 + be + (uint32_t)ne_t * (D + 1) * 2 + 3u * nlv * 4;
-        mbar_arrive_expect_tx(bar, total);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) bulk_g2s(sE + (size_t)f * mte, ed.field(f) + es, be, bar);
-        bulk_g2s(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar);
-        bulk_g2s(smem + L.a, a + es, be, bar);
-        bulk_g2s(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar);
+        mbar_init(bar + 1, 1);
+        // vertex tables first: the vertex gather below overlaps the element copy
+        mbar_arrive_expect_tx(bar, 3u * nlv * 4);
         bulk_g2s(smem + L.gid, td.lv_gid + vs, (uint32_t)nlv * 4, bar);
         bulk_g2s(smem + L.code, td.lv_code + vs, (uint32_t)nlv * 4, bar);
         bulk_g2s(smem + L.linc, td.lv_inc + vs, (uint32_t)nlv * 4, bar);
+        const uint32_t be = (uint32_t)ne_t * sizeof(T);
+        mbar_arrive_expect_tx(bar + 1, NF * be + (uint32_t)ne_t * 4 + be + (uint32_t)ne_t * (D + 1) * 2);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) bulk_g2s(sE + (size_t)f * mte, ed.field(f) + es, be, bar + 1);
+        bulk_g2s(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar + 1);
+        bulk_g2s(smem + L.a, a + es, be, bar + 1);
+        bulk_g2s(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1);
     }
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0)) {
-        if (threadIdx.x == 0) atomicOr(&sc->kerr, 1);
-        mbar_wait_bounded(bar, 0);  // give copies in flight a last chance before the CTA exits
+    // every thread takes the same decision, so no thread is left at a barrier
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+        if (threadIdx.x == 0) {
+            atomicOr(&sc->kerr, 1);
+            mbar_wait_bounded(bar, 0);  // give copies in flight a last chance before the CTA exits
+            mbar_wait_bounded(bar + 1, 0);
+        }
         return;
     }
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int64_t gid = sGid[k];
-        const bool fx = vd.fixed[gid] != 0;
+        const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             su[k * D + c] = u[gid * D + c];
             sv[k * D + c] = fx ? T(0) : v[gid * D + c];
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) {
+        if (threadIdx.x == 0) {
+            atomicOr(&sc->kerr, 1);
+            mbar_wait_bounded(bar + 1, 0);
+        }
+        return;
+    }
     const T mu = T(ph.mu), lam = T(ph.lam);
     const T sel = T(ph.s_el), kk = T(ph.k);
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
@@ -612,7 +627,7 @@ __global__ void __launch_bounds__(256) k_tile_hvp(TileDev td, ElemDev<T> ed, Ver
 #pragma unroll
                 for (int c = 0; c < D; ++c) acc[c] += m * sv[k * D + c];
             }
-            const bool fx = vd.fixed[gid] != 0;
+            const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 const T o = fx ? T(0) : acc[c];
@@ -791,15 +806,39 @@ size_t hvp_smem(const Ctx &c)
     return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv).total : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv).total;
 }
 
+// Resident CTAs per SM that the tile's shared memory allows (at most 4);
+// the kernel variant compiled for that count caps registers to match.
+template <typename T>
+int hvp_blocks_per_sm(const Ctx &c)
+{
+    const size_t per = hvp_smem<T>(c) + 1024;  // + static shared memory and reserve
+    int b = (int)((227 * 1024) / per);
+    return b < 1 ? 1 : (b > 4 ? 4 : b);
+}
+
+template <typename T, int D, bool CG, int MINB>
+static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+{
+    k_tile_hvp<T, D, CG, MINB><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y,
+                                                                               hp, c.partials, c.sc);
+}
+
 template <typename T, bool CG>
 static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
     c.n_launch += 1;
-    const size_t sm = hvp_smem<T>(c);
-    if (c.dim == 2)
-        k_tile_hvp<T, 2, CG><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
-    else
-        k_tile_hvp<T, 3, CG><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+    const int b = hvp_blocks_per_sm<T>(c);
+    if constexpr (sizeof(T) == 4) {
+        if (c.dim == 2)
+            (b >= 4 ? hvp_tile_v<T, 2, CG, 4> : hvp_tile_v<T, 2, CG, 3>)(c, ph, u, a, v, y, hp, s);
+        else
+            (b >= 4 ? hvp_tile_v<T, 3, CG, 4> : hvp_tile_v<T, 3, CG, 3>)(c, ph, u, a, v, y, hp, s);
+    } else {
+        if (c.dim == 2)
+            (b >= 2 ? hvp_tile_v<T, 2, CG, 2> : hvp_tile_v<T, 2, CG, 1>)(c, ph, u, a, v, y, hp, s);
+        else
+            (b >= 2 ? hvp_tile_v<T, 3, CG, 2> : hvp_tile_v<T, 3, CG, 1>)(c, ph, u, a, v, y, hp, s);
+    }
 }
 
 template <typename T, bool CG>
@@ -862,14 +901,16 @@ cudaError_t configure_elem_kernels()
     SET((k_tile_energy<3>));
     SET((k_tile_grad<2>));
     SET((k_tile_grad<3>));
-    SET((k_tile_hvp<float, 2, true>));
-    SET((k_tile_hvp<float, 3, true>));
-    SET((k_tile_hvp<float, 2, false>));
-    SET((k_tile_hvp<float, 3, false>));
-    SET((k_tile_hvp<double, 2, true>));
-    SET((k_tile_hvp<double, 3, true>));
-    SET((k_tile_hvp<double, 2, false>));
-    SET((k_tile_hvp<double, 3, false>));
+#define SET_HVP(T, MB)                    \
+    SET((k_tile_hvp<T, 2, true, MB>));    \
+    SET((k_tile_hvp<T, 3, true, MB>));    \
+    SET((k_tile_hvp<T, 2, false, MB>));   \
+    SET((k_tile_hvp<T, 3, false, MB>));
+    SET_HVP(float, 3)
+    SET_HVP(float, 4)
+    SET_HVP(double, 1)
+    SET_HVP(double, 2)
+#undef SET_HVP
     SET((k_tile_vjp<2>));
     SET((k_tile_vjp<3>));
 #undef SET

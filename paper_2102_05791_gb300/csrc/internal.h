@@ -18,8 +18,9 @@
 //     every vertex sum is formed in one fixed order (deterministic, no float
 //     atomics).
 //   * inc[tile_elem[t]*(dim+1) + s], s in [first, first+count) of lv_inc[lv],
-//     lists in increasing order the corners (local_elem*(dim+1) + corner)
-//     that touch local vertex lv.
+//     lists the corners that touch local vertex lv, in order of increasing
+//     local element, each encoded as its offset corner*dim*max_te +
+//     local_elem in the corner buffer; lv_inc also flags pinned vertices.
 //   * Per-tile ranges are padded to 16-byte multiples for bulk copies;
 //     padding elements have W = 0 and perm -1, padding local vertices have
 //     lv_code == LV_PAD and no incidences.

@@ -119,6 +119,7 @@ static int read_scalars(sim_handle *h, cudaStream_t s)
 {
     CK(h, cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
+    if (h->sc_host->kerr) return fail(h, SIM_ECUDA, "a kernel gave up waiting for its bulk copies");
     return SIM_OK;
 }
 
@@ -250,7 +251,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     // --- tiles
     int te = h->opt.tile_elems > 0 ? h->opt.tile_elems : (d == 3 ? 768 : 512);
     std::string terr;
-    if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, te, kMaxTileVerts, h->tb, terr))
+    if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, mesh->fixed, te, kMaxTileVerts, h->tb, terr))
         return fail(h, SIM_EINVAL, "tiling: " + terr);
     const TileBuild &tb = h->tb;
     const int64_t ne_int = tb.ne_int;

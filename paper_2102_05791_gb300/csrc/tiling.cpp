@@ -29,8 +29,8 @@ static uint64_t spread2(uint64_t x)
     return x;
 }
 
-bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, int te_max, int tv_max,
-                 TileBuild &out, std::string &err)
+bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
+                 int te_max, int tv_max, TileBuild &out, std::string &err)
 {
     const int nc = dim + 1;
     out = TileBuild();
@@ -107,6 +107,12 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     for (int ti = 0; ti < out.n_tiles; ++ti)
         out.tile_elem.push_back((int32_t)round_up(out.tile_elem.back() + (cut[ti + 1] - cut[ti]), kElemPad));
     out.ne_int = out.tile_elem.back();
+    for (int ti = 0; ti < out.n_tiles; ++ti)
+        out.max_te = std::max(out.max_te, out.tile_elem[ti + 1] - out.tile_elem[ti]);
+    if ((int64_t)(dim + 1) * dim * out.max_te > 65535) {
+        err = "tile too large for 16-bit corner offsets";
+        return false;
+    }
     out.perm.assign(out.ne_int, -1);
     for (int ti = 0; ti < out.n_tiles; ++ti)
         for (int i = cut[ti]; i < cut[ti + 1]; ++i) out.perm[out.tile_elem[ti] + (i - cut[ti])] = order[i];
@@ -125,7 +131,6 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
         const int nl = (int)verts.size();
         const int nl_pad = (int)round_up(nl, kVertPad);
-        out.max_te = std::max(out.max_te, out.tile_elem[ti + 1] - es);
         out.max_tv = std::max(out.max_tv, nl_pad);
         for (int j = 0; j < nl; ++j) {
             loc[verts[j]] = j;
@@ -145,12 +150,13 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         for (int j = 0; j < nl; ++j) bucket[j + 1] += bucket[j];
         const int64_t base = (int64_t)es * nc;
         for (int j = 0; j < nl; ++j)
-            out.lv_inc.push_back((uint32_t)bucket[j] | ((uint32_t)(bucket[j + 1] - bucket[j]) << 16));
+            out.lv_inc.push_back((uint32_t)bucket[j] | ((uint32_t)(bucket[j + 1] - bucket[j]) << 16) |
+                                 ((fixed && fixed[verts[j]]) ? kLvPinned : 0u));
         std::vector<int> fill(bucket.begin(), bucket.end() - 1);
         for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) {
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
-                out.inc[base + fill[l]++] = (uint16_t)((i - es) * nc + k);
+                out.inc[base + fill[l]++] = (uint16_t)(k * dim * out.max_te + (i - es));
             }
         for (int j = 0; j < nl; ++j) out.lv_gid.push_back(verts[j]);
         for (int j = nl; j < nl_pad; ++j) {
@@ -180,7 +186,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     out.lv_code.assign(out.lv_gid.size(), LV_PAD);
     for (int ti = 0; ti < out.n_tiles; ++ti)
         for (int j = out.tile_vert[ti]; j < out.tile_vert[ti + 1]; ++j) {
-            if ((out.lv_inc[j] >> 16) == 0) continue;  // padding entry
+            if (((out.lv_inc[j] >> 16) & kLvCountMask) == 0) continue;  // padding entry
             const int32_t v = out.lv_gid[j];
             if (cnt[v] == 1) {
                 out.lv_code[j] = LV_INTERIOR;

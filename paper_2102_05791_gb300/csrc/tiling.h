@@ -27,8 +27,8 @@ struct TileBuild {
     std::vector<int32_t> tile_elem;  // [n_tiles + 1] padded element offsets
     std::vector<int32_t> tile_vert;  // [n_tiles + 1] padded local-vertex offsets
     std::vector<int32_t> lv_gid, lv_code;
-    std::vector<uint32_t> lv_inc;    // (first incidence within the tile) | (count << 16)
-    std::vector<uint16_t> inc;       // [ne_int * (dim+1)]
+    std::vector<uint32_t> lv_inc;    // first incidence | count << 16 | kLvPinned
+    std::vector<uint16_t> inc;       // [ne_int * (dim+1)] corner offsets corner*dim*max_te + local elem
     std::vector<uint32_t> conn;      // [ne_int]
     std::vector<int32_t> fin_gid, fin_ptr;
 };
@@ -38,7 +38,7 @@ struct TileBuild {
 // te_max elements and at most tv_max (<= 256) distinct vertices.  `T` is
 // [ne][dim+1] in caller order.  Returns false and sets err if some vertex
 // belongs to no element or a single element exceeds the limits.
-bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, int te_max, int tv_max,
-                 TileBuild &out, std::string &err);
+bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
+                 int te_max, int tv_max, TileBuild &out, std::string &err);
 
 }  // namespace softsim

@@ -36,7 +36,7 @@ def main():
                         gravity=p.gravity, precision=args.precision, tile_elems=args.tile_elems,
                         threads=args.threads, device="cuda:0")
     rng = np.random.default_rng(0)
-    x = torch.from_numpy(p.X + 0.01 * rng.standard_normal(p.X.shape)).cuda()
+    x = torch.from_numpy(p.X + 1e-3 * rng.standard_normal(p.X.shape)).cuda()
     x[torch.from_numpy(p.fixed.astype(bool)).cuda()] = torch.from_numpy(p.X).cuda()[torch.from_numpy(p.fixed.astype(bool)).cuda()]
     a = torch.from_numpy(p.a).cuda()
     v = torch.from_numpy(rng.standard_normal(p.X.shape)).to(device="cuda", dtype=sim.vec_dtype)
