@@ -222,6 +222,27 @@ int sim_counters(const sim_handle *h, int64_t *kernel_launches);
 int sim_tile_stats(const sim_handle *h, int *n_tiles, double *elems_per_tile,
                    double *verts_per_tile, double *halo_fraction);
 
+/* Energy without allocation.  The paper has no counterpart: this is a
+ * deployment aid.  Returns in E_out (one device double) the quasistatic
+ * energy E(x, a) of sim_energy_grad for a mesh given entirely as
+ * caller-owned DEVICE arrays -- rest_pos, x [n_vert][dim] double, elems
+ * [n_elem][dim+1] int32, a [n_elem] double, fiber [n_elem][dim] double --
+ * with the scalars of `mat` (a host struct; its fiber and dt fields are
+ * ignored).  It needs no handle and allocates no device memory, for callers
+ * that cannot call cudaMalloc at that point: a process whose GPU memory is
+ * already claimed by another framework's pool allocator, or code that must
+ * not allocate after its setup.  Its scratch (block partial sums and a
+ * counter, about 33 KB) is a fixed array inside the library that every GPU
+ * loading the library keeps until exit.  At most 4,194,304 elements and
+ * vertices; larger meshes get SIM_EINVAL.  The first call on a device looks
+ * up the array's address (with that device current) and must come before
+ * any stream capture.  Calls share the array, so calls that overlap on the
+ * GPU race; serialise them.  Errors: sim_noalloc_last_error(). */
+int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const double *rest_pos,
+                       const int32_t *elems, const double *x, const double *a, const double *fiber,
+                       const sim_material *mat, double *E_out, void *stream);
+const char *sim_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

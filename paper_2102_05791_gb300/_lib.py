@@ -23,7 +23,7 @@ EXPORTED = [
     "sim_default_options", "sim_create", "sim_destroy", "sim_last_error", "sim_sizes",
     "sim_energy_grad", "sim_hvp", "sim_newton_solve", "sim_adjoint_solve", "sim_param_vjp",
     "sim_step_forward", "sim_step_backward", "sim_rollout", "sim_rollout_backward",
-    "sim_time_hvp", "sim_tile_stats", "sim_counters",
+    "sim_time_hvp", "sim_tile_stats", "sim_counters", "sim_energy_noalloc", "sim_noalloc_last_error",
 ]
 
 
@@ -86,9 +86,12 @@ def load(path: str | None = None):
     L.sim_rollout_backward.argtypes = [H, i, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_time_hvp.argtypes = [H, i, C.POINTER(C.c_float), vp]
     L.sim_counters.argtypes = [H, C.POINTER(C.c_int64)]
+    L.sim_energy_noalloc.argtypes = [i, C.c_int64, C.c_int64, vp, vp, vp, vp, vp, C.POINTER(SimMaterial), vp, vp]
+    L.sim_noalloc_last_error.argtypes = []
+    L.sim_noalloc_last_error.restype = C.c_char_p
     L.sim_tile_stats.argtypes = [H, C.POINTER(i), C.POINTER(d), C.POINTER(d), C.POINTER(d)]
     for name in EXPORTED:
-        if name != "sim_last_error":
+        if name not in ("sim_last_error", "sim_noalloc_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
