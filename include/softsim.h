@@ -207,11 +207,21 @@ int sim_rollout_backward(sim_handle *h, int n_steps, const double *a_seq, int ck
                          const double *vbarT, double *xbar0, double *vbar0, double *abar_seq,
                          double *seg_x, double *seg_v, sim_solve_stats *stats, void *stream);
 
-/* Kernel timer: launches the element HVP kernel n_launches times on the
- * handle's current internal state (after a solve) on `stream` and writes the
- * mean duration of one launch, in milliseconds, measured with CUDA events,
- * for the tile kernel (ms[0]) and the halo-finalise kernel (ms[1]). */
+/* Kernel timer: launches the element HVP kernel n_launches times back to
+ * back on the handle's current internal state (after a solve) on `stream`
+ * and writes the mean duration of one launch, in milliseconds, measured with
+ * CUDA events, for the tile kernel (ms[0]) and the halo-finalise kernel
+ * (ms[1]).  Back-to-back launches can find part of the previous launch's
+ * data in L2; sim_kernel_timing measures launches inside a solve. */
 int sim_time_hvp(sim_handle *h, int n_launches, float *ms, void *stream);
+
+/* In-solve kernel timing.  When switched on, the CG iterations of later
+ * solves record CUDA events around every HVP tile-kernel launch (on the
+ * launching stream, inside the captured graphs); sim_kernel_timing returns
+ * the summed duration in milliseconds and the number of timed launches since
+ * timing was last switched on (switching resets both). */
+int sim_set_kernel_timing(sim_handle *h, int on);
+int sim_kernel_timing(const sim_handle *h, double *hvp_tile_ms, int64_t *hvp_launches);
 
 /* Number of CUDA kernels the handle has launched so far (graph replays count
  * every kernel node they run). */

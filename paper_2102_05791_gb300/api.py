@@ -214,6 +214,15 @@ class Simulator:
         self._check("sim_time_hvp", self._lib.sim_time_hvp(self._h, int(n), ms, _stream()))
         return float(ms[0]), float(ms[1])
 
+    def set_kernel_timing(self, on=True):
+        self._check("sim_set_kernel_timing", self._lib.sim_set_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_timing(self):
+        """(summed ms, launches) of HVP tile kernels timed inside solves."""
+        ms, n = C.c_double(), C.c_int64()
+        self._lib.sim_kernel_timing(self._h, C.byref(ms), C.byref(n))
+        return float(ms.value), int(n.value)
+
     def kernel_launches(self):
         n = C.c_int64()
         self._lib.sim_counters(self._h, C.byref(n))

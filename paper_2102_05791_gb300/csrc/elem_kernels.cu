@@ -526,11 +526,12 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         bulk_g2s(smem + L.linc, td.lv_inc + vs, (uint32_t)nlv * 4, bar);
         const uint32_t be = (uint32_t)ne_t * sizeof(T);
         mbar_arrive_expect_tx(bar + 1, NF * be + (uint32_t)ne_t * 4 + be + (uint32_t)ne_t * (D + 1) * 2);
+        const uint64_t pol = l2_evict_first_policy();  // element data is read once per launch
 #pragma unroll
-        for (int f = 0; f < NF; ++f) bulk_g2s(sE + (size_t)f * mte, ed.field(f) + es, be, bar + 1);
-        bulk_g2s(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar + 1);
-        bulk_g2s(smem + L.a, a + es, be, bar + 1);
-        bulk_g2s(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1);
+        for (int f = 0; f < NF; ++f) bulk_g2s_stream(sE + (size_t)f * mte, ed.field(f) + es, be, bar + 1, pol);
+        bulk_g2s_stream(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar + 1, pol);
+        bulk_g2s_stream(smem + L.a, a + es, be, bar + 1, pol);
+        bulk_g2s_stream(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1, pol);
     }
     __syncthreads();
     // every thread takes the same decision, so no thread is left at a barrier
@@ -560,6 +561,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     }
     const T mu = T(ph.mu), lam = T(ph.lam);
     const T sel = T(ph.s_el), kk = T(ph.k);
+    T qsum = T(0);  // CG: sum of the element quadratic forms v_e . (H_e v_e) of this thread
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
         int lid[D + 1];
         unpack<D>(sConn[le], lid);
@@ -605,10 +607,17 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
                 for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
                 G[i][j] = W * (s + dvg[i] * gv[j]);
             }
+        if (CG) {
+            // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
+        }
         store_corners<T, D>(sE, mte, le, G);  // overwrites this element's own columns only
     }
     __syncthreads();
-    double dot = 0.0;
+    double dot = (double)qsum;
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int code = sCode[k];
         if (code == LV_PAD) continue;
@@ -629,19 +638,44 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             }
             const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const T o = fx ? T(0) : acc[c];
-                y[gid * D + c] = o;
-                if (CG) dot += (double)sv[k * D + c] * (double)o;
-            }
+            for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
         } else {
 #pragma unroll
             for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
+        }
+        if (CG && (code == LV_INTERIOR || (code & 1)) && (ph.kc > 0.0 || ph.dyn)) {
+            // per-vertex terms of p.Ap, counted once by the vertex's owner tile
+            double vt = 0.0;
+            if (ph.kc > 0.0) {
+                const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
+                const double pen = yy < 0.0 ? -yy : 0.0;
+                const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+                vt += ph.s_el * d2 * (double)sv[k * D + 1] * (double)sv[k * D + 1];
+            }
+            if (ph.dyn) {
+                double v2 = 0.0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) v2 += (double)sv[k * D + c] * (double)sv[k * D + c];
+                vt += vd.mass[gid] * v2;
+            }
+            dot += vt;
         }
     }
     if (CG) {
         const double s = block_sum(dot);
         if (threadIdx.x == 0) partials[t] = s;
+        if (last_block(&sc->ticket[TK_FIN], gridDim.x)) {
+            const double pAp = sum_partials(partials, gridDim.x);
+            if (threadIdx.x == 0) {
+                sc->pAp = pAp;
+                if (pAp > 0.0 && isfinite(pAp)) {
+                    sc->alpha = sc->rr / pAp;
+                } else {
+                    sc->alpha = 0.0;
+                    sc->negcurv = 1;
+                }
+            }
+        }
     }
 }
 
@@ -865,6 +899,12 @@ void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v
 }
 
 template <typename T>
+void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+{
+    hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
+}
+
+template <typename T>
 void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
                           cudaStream_t s)
 {
@@ -921,6 +961,10 @@ template void launch_hvp<float>(const Ctx &, const Phys &, const float *, const 
                                 float *, bool, cudaStream_t);
 template void launch_hvp<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
                                  double *, double *, bool, cudaStream_t);
+template void launch_hvp_cg<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
+                                   float *, cudaStream_t);
+template void launch_hvp_cg<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
+                                    double *, double *, cudaStream_t);
 template void launch_hvp_tile_only<float>(const Ctx &, const Phys &, const float *, const float *, const float *,
                                           float *, float *, cudaStream_t);
 template void launch_hvp_tile_only<double>(const Ctx &, const Phys &, const double *, const double *,

@@ -51,6 +51,7 @@ struct TileDev {
     const int32_t *perm = nullptr;       // [ne_int] tile order -> caller order, -1 = padding
     const int32_t *fin_gid = nullptr;    // [n_fin]
     const int32_t *fin_ptr = nullptr;    // [n_fin + 1]
+    const int32_t *vfin = nullptr;       // [nv] halo index of a vertex, -1 if one tile owns it
 };
 
 template <typename T>
@@ -160,6 +161,16 @@ void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p
                     int max_iter, cudaStream_t s);
 template <typename T>
 void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStream_t s);
+// CG update that first completes A p: vertices of one tile take it from Ap
+// (written by the HVP tile kernel), halo vertices add their partial sums hp
+// and their per-vertex terms; then d += alpha p, r -= alpha A p, r.r, beta.
+template <typename T>
+void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
+                           const T *hp, cudaStream_t s);
+// HVP tile kernel of the CG loop: A p for single-tile vertices, halo
+// partials, and p.Ap from element quadratic forms -> alpha (no finalize).
+template <typename T>
+void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>
 void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s);
 template <typename T>

@@ -74,18 +74,42 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int n_
 }
 
 // Fixed-order sum of n partials (bypassing L1: they were written by other
-// blocks); valid in thread 0.
+// blocks); valid in thread 0.  Each thread keeps 8 loads in flight with 8
+// accumulators that always take the same indices, so the result does not
+// depend on timing.
 __device__ __forceinline__ double sum_partials(const double *p, int n)
 {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(p + i);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int bd = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 7 * bd < n; i += 8 * bd) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + i + k * bd);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += v[k];
+    }
+    for (; i < n; i += bd) acc[0] += __ldcg(p + i);
+    const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     return block_sum(s);
 }
 
 __device__ __forceinline__ double min_partials(const double *p, int n)
 {
-    double s = INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmin(s, __ldcg(p + i));
+    double acc[8] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    const int bd = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 7 * bd < n; i += 8 * bd) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + i + k * bd);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = fmin(acc[k], v[k]);
+    }
+    for (; i < n; i += bd) acc[0] = fmin(acc[0], __ldcg(p + i));
+    double s = acc[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) s = fmin(s, acc[k]);
     return block_min(s);
 }
 

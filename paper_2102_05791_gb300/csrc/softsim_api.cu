@@ -54,7 +54,11 @@ struct sim_handle {
     DevScalars *sc_host = nullptr;  // pinned mirror
     cudaStream_t cap = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    Graph cg_graph[2];              // [dyn]
+    Graph cg_graph[2][2];           // [dyn][kernel timing]
+    int timing = 0;                 // record events around HVP tile launches in solves
+    cudaEvent_t tev[2 * kCgBlock] = {};
+    double t_hvp_ms = 0.0;          // accumulated in-solve HVP tile-kernel time
+    int64_t n_hvp_timed = 0;
     std::string err;
 };
 
@@ -172,8 +176,11 @@ extern "C" int sim_tile_stats(const sim_handle *h, int *n_tiles, double *ept, do
 extern "C" int sim_destroy(sim_handle *h)
 {
     if (!h) return SIM_EINVAL;
-    for (auto &gr : h->cg_graph)
-        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    for (auto &row : h->cg_graph)
+        for (auto &gr : row)
+            if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    for (auto &e : h->tev)
+        if (e) cudaEventDestroy(e);
     for (void *p : h->allocs) cudaFree(p);
     if (h->sc_host) cudaFreeHost(h->sc_host);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -249,7 +256,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
         for (int64_t i = 0; i < nv; ++i) fixed[i] = mesh->fixed[i] ? 1 : 0;
 
     // --- tiles
-    int te = h->opt.tile_elems > 0 ? h->opt.tile_elems : (d == 3 ? 768 : 512);
+    int te = h->opt.tile_elems > 0 ? h->opt.tile_elems : (d == 3 ? 384 : 512);
     std::string terr;
     if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, mesh->fixed, te, kMaxTileVerts, h->tb, terr))
         return fail(h, SIM_EINVAL, "tiling: " + terr);
@@ -344,7 +351,8 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if ((rc = upload(h, tb.perm, &td.perm))) return rc;
     if ((rc = upload(h, tb.fin_gid, &td.fin_gid))) return rc;
     if ((rc = upload(h, tb.fin_ptr, &td.fin_ptr))) return rc;
-    c.threads = h->opt.threads > 0 ? h->opt.threads : 256;
+    if ((rc = upload(h, tb.vfin, &td.vfin))) return rc;
+    c.threads = h->opt.threads > 0 ? h->opt.threads : (d == 3 ? 128 : 256);
     if (c.threads % 32 || c.threads > 256) return fail(h, SIM_EINVAL, "threads must be a multiple of 32, at most 256");
     c.n_fin_blocks = std::max(1, (td.n_fin + 255) / 256);
 
@@ -464,8 +472,10 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
 {
     T *d = (T *)h->vd, *r = (T *)h->vr, *p = (T *)h->vp, *Ap = (T *)h->vAp;
     for (int k = 0; k < kCgBlock; ++k) {
-        launch_hvp<T>(h->ctx, ph, View<T>::u(h), View<T>::a(h), p, Ap, View<T>::hp(h), true, s);
-        launch_cg_update<T>(h->ctx, d, r, p, Ap, s);
+        if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
+        launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), View<T>::a(h), p, Ap, View<T>::hp(h), s);
+        if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k + 1], s, cudaEventRecordExternal);
+        launch_cg_update_halo<T>(h->ctx, ph, View<T>::u(h), d, r, p, Ap, View<T>::hp(h), s);
         launch_cg_dir<T>(h->ctx, p, r, s);
     }
 }
@@ -473,7 +483,7 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
 template <typename T>
 static int get_cg_graph(sim_handle *h, const Phys &ph, cudaGraphExec_t *exec)
 {
-    Graph &gr = h->cg_graph[ph.dyn ? 1 : 0];
+    Graph &gr = h->cg_graph[ph.dyn ? 1 : 0][h->timing ? 1 : 0];
     if (!gr.valid) {
         cudaGraph_t graph = nullptr;
         CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
@@ -505,9 +515,22 @@ static int run_cg(sim_handle *h, const Phys &ph, int max_iter, cudaStream_t s)
     if ((rc = read_scalars(h, s))) return rc;
     const int max_blocks = max_iter / kCgBlock + 2;
     for (int b = 0; b < max_blocks && !h->sc_host->done; ++b) {
+        const int it0 = h->sc_host->iter;
+        const int neg0 = h->sc_host->negcurv;
         CK(h, cudaGraphLaunch(exec, s));
-        h->ctx.n_launch += 4 * kCgBlock;
+        h->ctx.n_launch += 3 * kCgBlock;
         if ((rc = read_scalars(h, s))) return rc;
+        if (h->timing) {
+            // tile launches that did work in this replay (later ones exit at once)
+            int active = h->sc_host->iter - it0 + ((h->sc_host->negcurv && !neg0) ? 1 : 0);
+            active = std::min(active, kCgBlock);
+            for (int k = 0; k < active; ++k) {
+                float ms = 0.f;
+                CK(h, cudaEventElapsedTime(&ms, h->tev[2 * k], h->tev[2 * k + 1]));
+                h->t_hvp_ms += ms;
+            }
+            h->n_hvp_timed += active;
+        }
     }
     if (!h->sc_host->done) return fail(h, SIM_ECUDA, "CG control did not terminate");
     return SIM_OK;
@@ -949,6 +972,25 @@ extern "C" int sim_rollout_backward(sim_handle *h, int n_steps, const double *a_
     CK(h, cudaMemcpyAsync(vbar0, h->rv[cur], bytes, cudaMemcpyDeviceToDevice, s));
     CK(h, cudaStreamSynchronize(s));
     if (st) *st = acc;
+    return SIM_OK;
+}
+
+extern "C" int sim_set_kernel_timing(sim_handle *h, int on)
+{
+    CHECK_H(h);
+    if (on && !h->tev[0])
+        for (auto &e : h->tev) CK(h, cudaEventCreate(&e));
+    h->timing = on ? 1 : 0;
+    h->t_hvp_ms = 0.0;
+    h->n_hvp_timed = 0;
+    return SIM_OK;
+}
+
+extern "C" int sim_kernel_timing(const sim_handle *h, double *hvp_tile_ms, int64_t *hvp_launches)
+{
+    if (!h) return SIM_EINVAL;
+    if (hvp_tile_ms) *hvp_tile_ms = h->t_hvp_ms;
+    if (hvp_launches) *hvp_launches = h->n_hvp_timed;
     return SIM_OK;
 }
 

@@ -182,6 +182,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         }
     }
     out.n_slots = out.fin_ptr.back();
+    out.vfin = fin_index;
     std::vector<int32_t> next(out.fin_ptr.begin(), out.fin_ptr.end() - 1);
     out.lv_code.assign(out.lv_gid.size(), LV_PAD);
     for (int ti = 0; ti < out.n_tiles; ++ti)

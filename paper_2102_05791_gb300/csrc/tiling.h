@@ -31,6 +31,7 @@ struct TileBuild {
     std::vector<uint16_t> inc;       // [ne_int * (dim+1)] corner offsets corner*dim*max_te + local elem
     std::vector<uint32_t> conn;      // [ne_int]
     std::vector<int32_t> fin_gid, fin_ptr;
+    std::vector<int32_t> vfin;       // [nv] index into fin_gid, or -1 for a vertex of one tile
 };
 
 // Orders the elements along a Morton curve of their centroids (cells of the

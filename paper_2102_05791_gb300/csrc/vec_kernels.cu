@@ -86,6 +86,79 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, T *__restrict__ d,
     }
 }
 
+// d += alpha p, r -= alpha A p, r.r -> beta / done, with A p completed here for
+// halo vertices (partial sums in tile order + per-vertex terms).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, Phys ph, const T *__restrict__ u,
+                                                        T *__restrict__ d, T *__restrict__ r, const T *__restrict__ p,
+                                                        const T *__restrict__ Ap, const T *__restrict__ hp,
+                                                        double *__restrict__ partials, DevScalars *sc)
+{
+    if (sc->done) return;
+    const bool neg = sc->negcurv != 0;
+    const bool first = sc->iter == 0;
+    const T alpha = T(sc->alpha);
+    float rr32 = 0.0f;  // at most a few vertices per thread; summed in FP64 across threads
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vd.nv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (neg) {
+            if (first)
+#pragma unroll
+                for (int c = 0; c < D; ++c) d[i * D + c] = p[i * D + c];
+            continue;
+        }
+        T a[D];
+        const int f = td.vfin[i];
+        if (f < 0) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) a[c] = Ap[i * D + c];
+        } else {
+            const bool fx = vd.fixed[i] != 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) a[c] = T(0);
+            for (int s = td.fin_ptr[f]; s < td.fin_ptr[f + 1]; ++s)
+#pragma unroll
+                for (int c = 0; c < D; ++c) a[c] += hp[(int64_t)s * D + c];
+            if (ph.kc > 0.0) {
+                const double yy = vd.X[i * D + 1] + (double)u[i * D + 1];
+                const double pen = yy < 0.0 ? -yy : 0.0;
+                const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+                a[1] += T(ph.s_el * d2) * p[i * D + 1];
+            }
+            if (ph.dyn) {
+                const T m = T(vd.mass[i]);
+#pragma unroll
+                for (int c = 0; c < D; ++c) a[c] += m * p[i * D + c];
+            }
+            if (fx)
+#pragma unroll
+                for (int c = 0; c < D; ++c) a[c] = T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            d[i * D + c] += alpha * p[i * D + c];
+            const T ri = r[i * D + c] - alpha * a[c];
+            r[i * D + c] = ri;
+            rr32 += (float)ri * (float)ri;
+        }
+    }
+    const double s = block_sum((double)rr32);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->ticket[TK_CG], gridDim.x)) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            if (neg) {
+                sc->done = 1;
+            } else {
+                sc->beta = tot / sc->rr;
+                sc->rr = tot;
+                sc->iter += 1;
+                if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, const T *__restrict__ r,
                                                 const DevScalars *sc)
@@ -277,6 +350,18 @@ void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStr
 }
 
 template <typename T>
+void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
+                           const T *hp, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const int g = vec_grid(c.nv * 4);
+    if (c.dim == 2)
+        k_cg_update_halo<T, 2><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
+    else
+        k_cg_update_halo<T, 3><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
+}
+
+template <typename T>
 void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s)
 {
     c.n_launch += 1;
@@ -363,6 +448,8 @@ int vec_grid_size(int64_t n) { return vec_grid(n); }
 #define INST(T)                                                                                                     \
     template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, cudaStream_t); \
     template void launch_cg_update<T>(const Ctx &, T *, T *, const T *, const T *, cudaStream_t);                   \
+    template void launch_cg_update_halo<T>(const Ctx &, const Phys &, const T *, T *, T *, const T *, const T *,    \
+                                           const T *, cudaStream_t);                                                \
     template void launch_cg_dir<T>(const Ctx &, T *, const T *, cudaStream_t);                                      \
     template void launch_dir_check<T>(const Ctx &, const double *, T *, cudaStream_t);                              \
     template void launch_step_update<T>(const Ctx &, double *, const T *, double, float *, cudaStream_t);           \
