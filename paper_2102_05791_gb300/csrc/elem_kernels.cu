@@ -663,19 +663,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     }
     if (CG) {
         const double s = block_sum(dot);
-        if (threadIdx.x == 0) partials[t] = s;
-        if (last_block(&sc->ticket[TK_FIN], gridDim.x)) {
-            const double pAp = sum_partials(partials, gridDim.x);
-            if (threadIdx.x == 0) {
-                sc->pAp = pAp;
-                if (pAp > 0.0 && isfinite(pAp)) {
-                    sc->alpha = sc->rr / pAp;
-                } else {
-                    sc->alpha = 0.0;
-                    sc->negcurv = 1;
-                }
-            }
-        }
+        if (threadIdx.x == 0) partials[t] = s;  // reduced by k_cg_alpha
     }
 }
 
@@ -902,6 +890,7 @@ template <typename T>
 void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
     hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
+    launch_cg_alpha(c, c.td.n_tiles, s);
 }
 
 template <typename T>

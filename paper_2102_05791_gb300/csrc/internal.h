@@ -168,7 +168,8 @@ template <typename T>
 void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
                            const T *hp, cudaStream_t s);
 // HVP tile kernel of the CG loop: A p for single-tile vertices, halo
-// partials, and p.Ap from element quadratic forms -> alpha (no finalize).
+// partials, and p.Ap partials from element quadratic forms, followed by the
+// one-block reduction to alpha (no finalize).
 template <typename T>
 void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>
@@ -196,6 +197,8 @@ void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, d
                      cudaStream_t s);
 // v1 = (x1 - x0)/dt
 int vec_grid_size(int64_t n);
+// one block: alpha from the n_partials p.Ap partials of the HVP tile kernel
+void launch_cg_alpha(const Ctx &c, int n_partials, cudaStream_t s);
 // r = b - Ax, |r|^2 -> sc->gn2
 void launch_residual(const Ctx &c, const double *b, const double *Ax, double *r, cudaStream_t s);
 // x += d

@@ -59,12 +59,15 @@ __device__ __forceinline__ double block_min(double v)
 
 // Call after thread 0 has written this block's partial(s).  Returns true in
 // every thread of the block that arrives last; that block resets the ticket.
+// Only the partials (written by thread 0) must be visible to the last block,
+// so only thread 0 fences before taking its ticket.
 __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int n_blocks)
 {
     __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == n_blocks - 1);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        is_last = (atomicAdd(ticket, 1u) == n_blocks - 1);
+    }
     __syncthreads();
     if (is_last) {
         __threadfence();

@@ -518,7 +518,7 @@ static int run_cg(sim_handle *h, const Phys &ph, int max_iter, cudaStream_t s)
         const int it0 = h->sc_host->iter;
         const int neg0 = h->sc_host->negcurv;
         CK(h, cudaGraphLaunch(exec, s));
-        h->ctx.n_launch += 3 * kCgBlock;
+        h->ctx.n_launch += 5 * kCgBlock;
         if ((rc = read_scalars(h, s))) return rc;
         if (h->timing) {
             // tile launches that did work in this replay (later ones exit at once)

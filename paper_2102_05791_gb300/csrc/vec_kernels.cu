@@ -143,18 +143,38 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
         }
     }
     const double s = block_sum((double)rr32);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-    if (last_block(&sc->ticket[TK_CG], gridDim.x)) {
-        const double tot = sum_partials(partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            if (neg) {
-                sc->done = 1;
-            } else {
-                sc->beta = tot / sc->rr;
-                sc->rr = tot;
-                sc->iter += 1;
-                if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
-            }
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;  // reduced by k_cg_beta
+}
+
+// One block: p.Ap from the HVP tile partials -> alpha (or non-positive curvature).
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ partials, int n, DevScalars *sc)
+{
+    if (sc->done) return;
+    const double pAp = sum_partials(partials, n);
+    if (threadIdx.x == 0) {
+        sc->pAp = pAp;
+        if (pAp > 0.0 && isfinite(pAp)) {
+            sc->alpha = sc->rr / pAp;
+        } else {
+            sc->alpha = 0.0;
+            sc->negcurv = 1;
+        }
+    }
+}
+
+// One block: r.r from the update partials -> beta, iteration count, done.
+__global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ partials, int n, DevScalars *sc)
+{
+    if (sc->done) return;
+    const double tot = sum_partials(partials, n);
+    if (threadIdx.x == 0) {
+        if (sc->negcurv) {
+            sc->done = 1;
+        } else {
+            sc->beta = tot / sc->rr;
+            sc->rr = tot;
+            sc->iter += 1;
+            if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
         }
     }
 }
@@ -353,12 +373,19 @@ template <typename T>
 void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
                            const T *hp, cudaStream_t s)
 {
-    c.n_launch += 1;
+    c.n_launch += 2;
     const int g = vec_grid(c.nv * 4);
     if (c.dim == 2)
         k_cg_update_halo<T, 2><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
     else
         k_cg_update_halo<T, 3><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
+    k_cg_beta<<<1, 1024, 0, s>>>(c.partials, g, c.sc);
+}
+
+void launch_cg_alpha(const Ctx &c, int n_partials, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_cg_alpha<<<1, 1024, 0, s>>>(c.partials, n_partials, c.sc);
 }
 
 template <typename T>
