@@ -232,6 +232,43 @@ int sim_counters(const sim_handle *h, int64_t *kernel_launches);
 int sim_tile_stats(const sim_handle *h, int *n_tiles, double *elems_per_tile,
                    double *verts_per_tile, double *halo_fraction);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent meshes of uneven size (same dim; materials may differ
+ * only in mu and lambda), each rolled out for n_steps backward-Euler steps
+ * (Eq. opt-be) and differentiated by backpropagation through time, in ONE
+ * persistent kernel launch replayed from a captured CUDA graph.  Each CTA
+ * takes the next mesh (largest first) and runs its whole forward rollout
+ * (Newton-CG per step) and backward pass (refined adjoint CG and parameter
+ * VJP per step, Eq. dLda-re-ordered) with block-level synchronisation only.
+ * Mixed precision as SIM_PREC_MIXED.  Deterministic: a mesh is always
+ * computed by one CTA with a fixed thread count and fixed-order sums. */
+typedef struct sim_batch sim_batch;
+
+/* Meshes, materials (dt > 0) and options as for sim_create, HOST arrays,
+ * copied.  Vertices and elements of mesh m follow those of meshes 0..m-1 in
+ * every concatenated array below. */
+int sim_batch_create(int n_meshes, const sim_mesh *meshes, const sim_material *mats,
+                     const sim_options *opt, sim_batch **out);
+int sim_batch_destroy(sim_batch *b);
+const char *sim_batch_last_error(const sim_batch *b);
+int sim_batch_sizes(const sim_batch *b, int *n_meshes, int64_t *total_vert, int64_t *total_elem);
+
+/* Forward rollout and BPTT of every mesh.  DEVICE arrays, V/E = total
+ * vertices/elements, d = dim:
+ *   states_x, states_v [n_steps+1][V][d]: slot 0 holds the initial state on
+ *     entry; slots 1..n_steps receive the states x_t, v_t;
+ *   a_seq [n_steps][E] activations per step;
+ *   xbarT, vbarT [V][d] = dL/dx_T, dL/dv_T;
+ *   abar_seq [n_steps][E] receives dL/da_t; xbar0, vbar0 [V][d] receive
+ *     dL/dx_0, dL/dv_0;
+ *   mesh_stats [n_meshes][4] ints (or NULL): status, Newton iterations, CG
+ *     iterations forward, CG iterations adjoint.
+ * Stream-ordered; returns after enqueueing (synchronise before reading). */
+int sim_batch_rollout(sim_batch *b, int n_steps, double *states_x, double *states_v,
+                      const double *a_seq, const double *xbarT, const double *vbarT,
+                      double *abar_seq, double *xbar0, double *vbar0, int *mesh_stats,
+                      void *stream);
+
 /* Energy without allocation.  The paper has no counterpart: this is a
  * deployment aid.  Returns in E_out (one device double) the quasistatic
  * energy E(x, a) of sim_energy_grad for a mesh given entirely as

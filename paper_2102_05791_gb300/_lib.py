@@ -25,6 +25,7 @@ EXPORTED = [
     "sim_step_forward", "sim_step_backward", "sim_rollout", "sim_rollout_backward",
     "sim_time_hvp", "sim_tile_stats", "sim_counters", "sim_energy_noalloc", "sim_noalloc_last_error",
     "sim_set_kernel_timing", "sim_kernel_timing",
+    "sim_batch_create", "sim_batch_destroy", "sim_batch_last_error", "sim_batch_sizes", "sim_batch_rollout",
 ]
 
 
@@ -93,8 +94,14 @@ def load(path: str | None = None):
     L.sim_noalloc_last_error.argtypes = []
     L.sim_noalloc_last_error.restype = C.c_char_p
     L.sim_tile_stats.argtypes = [H, C.POINTER(i), C.POINTER(d), C.POINTER(d), C.POINTER(d)]
+    L.sim_batch_create.argtypes = [i, C.POINTER(SimMesh), C.POINTER(SimMaterial), C.POINTER(SimOptions), C.POINTER(H)]
+    L.sim_batch_destroy.argtypes = [H]
+    L.sim_batch_last_error.argtypes = [H]
+    L.sim_batch_last_error.restype = C.c_char_p
+    L.sim_batch_sizes.argtypes = [H, C.POINTER(i), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.sim_batch_rollout.argtypes = [H, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:
-        if name not in ("sim_last_error", "sim_noalloc_last_error"):
+        if name not in ("sim_last_error", "sim_noalloc_last_error", "sim_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -235,6 +235,84 @@ class Simulator:
         return {"n_tiles": n.value, "elems_per_tile": e.value, "verts_per_tile": v.value, "halo_fraction": hf.value}
 
 
+class Batch:
+    """Many meshes rolled out and differentiated in one persistent launch (sim_batch_*).
+
+    ``problems`` are dicts or objects with X, T, fixed, fiber, mu, lam and the
+    shared scalars (k_muscle, density, gravity, k_contact, contact_power,
+    log_mode, dt).  Concatenated layouts follow include/softsim.h.
+    """
+
+    def __init__(self, problems, newton_rtol=1e-8, adjoint_rtol=1e-6, max_newton=100, max_cg=500,
+                 max_adjoint_cg=2000, max_ls=30, device=None):
+        self._lib = L.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._keep = []
+        n = len(problems)
+        meshes = (L.SimMesh * n)()
+        mats = (L.SimMaterial * n)()
+        for i, p in enumerate(problems):
+            X = np.ascontiguousarray(p.X, dtype=np.float64)
+            T = np.ascontiguousarray(p.T, dtype=np.int32)
+            fx = np.ascontiguousarray(p.fixed, dtype=np.uint8)
+            fb = np.ascontiguousarray(p.fiber, dtype=np.float64)
+            self._keep += [X, T, fx, fb]
+            meshes[i] = L.SimMesh(X.shape[1], X.shape[0], T.shape[0], X.ctypes.data, T.ctypes.data, fx.ctypes.data)
+            mats[i] = L.SimMaterial(p.mu, p.lam, p.k_muscle, p.density, p.gravity, p.k_contact, p.contact_power,
+                                    p.log_mode, p.dt, fb.ctypes.data)
+        opt = L.SimOptions()
+        self._lib.sim_default_options(C.byref(opt))
+        opt.newton_rtol, opt.adjoint_rtol = float(newton_rtol), float(adjoint_rtol)
+        opt.max_newton, opt.max_cg, opt.max_adjoint_cg, opt.max_ls = int(max_newton), int(max_cg), int(max_adjoint_cg), int(max_ls)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.sim_batch_create(n, meshes, mats, C.byref(opt), C.byref(h))
+        if rc != 0:
+            raise SimError("sim_batch_create", rc, self._lib.sim_batch_last_error(None).decode())
+        self._h = h
+        self._keep = []
+        nm, V, E = C.c_int(), C.c_int64(), C.c_int64()
+        self._lib.sim_batch_sizes(h, C.byref(nm), C.byref(V), C.byref(E))
+        self.n_meshes, self.V, self.E = nm.value, V.value, E.value
+        self.dim = problems[0].X.shape[1]
+        self.vert_offsets = np.concatenate([[0], np.cumsum([p.X.shape[0] for p in problems])])
+        self.elem_offsets = np.concatenate([[0], np.cumsum([p.T.shape[0] for p in problems])])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sim_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rollout(self, x0, v0, a_seq, xbarT, vbarT, states=None):
+        """Forward rollout + BPTT of every mesh.  Returns (states_x, states_v,
+        abar_seq, xbar0, vbar0, mesh_stats) as device tensors."""
+        n_steps = int(a_seq.shape[0])
+        if states is None:
+            sx = torch.empty((n_steps + 1, self.V, self.dim), dtype=torch.float64, device=self.device)
+            sv = torch.empty_like(sx)
+        else:
+            sx, sv = states
+        sx[0].copy_(x0)
+        sv[0].copy_(v0)
+        a_seq = a_seq.contiguous()
+        abar = torch.empty_like(a_seq)
+        xb0 = torch.empty((self.V, self.dim), dtype=torch.float64, device=self.device)
+        vb0 = torch.empty_like(xb0)
+        ms = torch.zeros((self.n_meshes, 4), dtype=torch.int32, device=self.device)
+        rc = self._lib.sim_batch_rollout(self._h, n_steps, _ptr(sx), _ptr(sv), _ptr(a_seq),
+                                         _ptr(xbarT.contiguous()), _ptr(vbarT.contiguous()), _ptr(abar), _ptr(xb0),
+                                         _ptr(vb0), _ptr(ms), _stream())
+        if rc != 0:
+            raise SimError("sim_batch_rollout", rc, self._lib.sim_batch_last_error(self._h).decode())
+        return sx, sv, abar, xb0, vb0, ms
+
+
 # ---------------------------------------------------------------- autograd
 
 class QuasistaticSolve(torch.autograd.Function):

@@ -1,0 +1,71 @@
+"""Batched persistent rollouts (many meshes, one launch) vs the oracle's
+per-mesh backward-Euler rollout and BPTT (Eq. opt-be, Eq. dLda-re-ordered).
+
+Tolerances: states within 1e-6 of the displacement scale (both converge to
+|g| <= 1e-8 |g0| per step); gradients within 1e-4 relative L2 (mixed
+precision with FP64-refined adjoints)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from simhelp import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _meshes():
+    out = []
+    for i, (nx, ny, mu) in enumerate([(4, 2, 1e4), (7, 3, 7e3), (5, 2, 1.6e4), (9, 4, 5.5e3)]):
+        p = synth.make_small2d(nx, ny, fix_bottom=False, seed=60 + i)
+        p.k_contact, p.contact_power, p.dt = 1e6, 3, 1.0 / 30.0
+        p.mu, p.lam = mu, 4.0 * mu
+        out.append(p)
+    return out
+
+
+def test_batch_rollout_matches_oracle_and_is_deterministic():
+    from paper_2102_05791_gb300.api import Batch
+    probs = _meshes()
+    b = Batch(probs, adjoint_rtol=1e-8)
+    rng = np.random.default_rng(70)
+    nT = 3
+    E = b.E
+    a_seq = rng.uniform(0.0, 1.0, size=(nT, E))
+    x0 = np.concatenate([p.X for p in probs])
+    v0 = 0.1 * rng.standard_normal(x0.shape)
+    xbT = rng.standard_normal(x0.shape)
+    vbT = 0.01 * rng.standard_normal(x0.shape)
+    sx, sv, abar, xb0, vb0, ms = b.rollout(dev(x0), dev(v0), dev(a_seq), dev(xbT), dev(vbT))
+    torch.cuda.synchronize()
+    ms = host(ms)
+    assert (ms[:, 0] == 0).all(), ms
+    sx, abar, xb0, vb0 = host(sx), host(abar), host(xb0), host(vb0)
+    vo, eo = b.vert_offsets, b.elem_offsets
+    for i, p in enumerate(probs):
+        m = oracle.make_model(p)
+        vs_, ve_ = vo[i], vo[i + 1]
+        es_, ee_ = eo[i], eo[i + 1]
+        a_i = a_seq[:, es_:ee_]
+        xs, vs = oracle.rollout(m, x0[vs_:ve_], v0[vs_:ve_], a_i, rtol=1e-10)
+        scale = max(np.abs(xs[-1] - xs[0]).max(), 1e-6)
+        assert np.abs(sx[-1, vs_:ve_] - xs[-1]).max() <= 1e-6 * scale
+        xb, vb, ab = oracle.rollout_backward(m, xs, vs, a_i, xbT[vs_:ve_], vbT[vs_:ve_])
+        assert np.linalg.norm(abar[:, es_:ee_] - ab) <= 1e-4 * np.linalg.norm(ab)
+        assert np.linalg.norm(vb0[vs_:ve_] - vb) <= 1e-4 * np.linalg.norm(vb)
+        assert np.linalg.norm(xb0[vs_:ve_] - xb) <= 1e-4 * np.linalg.norm(xb)
+    # same inputs, second launch (graph replay): bit-identical
+    sx2, sv2, abar2, xb02, vb02, ms2 = b.rollout(dev(x0), dev(v0), dev(a_seq), dev(xbT), dev(vbT))
+    torch.cuda.synchronize()
+    assert np.array_equal(host(abar2), abar)
+    assert np.array_equal(host(sx2), sx)
+    b.close()
+
+
+def test_batch_rejects_mixed_dims_and_materials():
+    from paper_2102_05791_gb300.api import Batch, SimError
+    probs = _meshes()[:2]
+    probs[1].k_muscle = 1.0
+    with pytest.raises(SimError):
+        Batch(probs)
