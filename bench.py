@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", choices=["c5", "c3", "c5_eighth"], default="c5")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 1,024-body measurement")
     return ap.parse_args()
 
 
@@ -63,6 +64,90 @@ def workload(name):
     if name == "c5_eighth":
         return synth.make_config5(2), "box 4x2x2, 64x32x32 hex x 6 tets (393,216 tets), quasistatic Newton-CG + adjoint + VJP"
     return synth.make_config3(), "box 2x1x1, 32x16x16 hex x 5 tets (40,960 tets), quasistatic Newton-CG + adjoint + VJP"
+
+
+def c4_inputs(n_meshes=1024, n_steps=60):
+    """1,024 2D bodies (tris log-uniform in [200, 8000], mu ~ U(5e3, 2e4)),
+    60 backward-Euler steps, loss = mean horizontal position of each body at
+    the end (dL/dx_T = e_x / n_vert per body)."""
+    import synth
+    probs = synth.make_config4(n_meshes, n_steps)
+    x0 = np.concatenate([p.X for p in probs])
+    a_seq = np.concatenate([p.extra["a_seq"] for p in probs], axis=1)
+    xbT = np.zeros_like(x0)
+    off = 0
+    for p in probs:
+        xbT[off:off + p.n_vert, 0] = 1.0 / p.n_vert
+        off += p.n_vert
+    return probs, x0, a_seq, xbT
+
+
+def run_batched(dev, steps, warmup, plain_sample=8):
+    """Config 4: one batched launch (forward + BPTT of every body) vs the plain
+    per-mesh FP64 path (sim_rollout + sim_rollout_backward per body) on a
+    sample of bodies spread over the size range.  A solve = one body-step,
+    forward Newton solve plus adjoint solve."""
+    import torch
+    from paper_2102_05791_gb300 import api
+    probs, x0, a_seq, xbT = c4_inputs()
+    n_steps = a_seq.shape[0]
+    bt = api.Batch(probs, newton_rtol=1e-8, adjoint_rtol=1e-6, device=dev)
+    X0 = torch.from_numpy(x0).to(dev)
+    V0 = torch.zeros_like(X0)
+    A = torch.from_numpy(a_seq).to(dev)
+    XB = torch.from_numpy(xbT).to(dev)
+    VB = torch.zeros_like(X0)
+    states = (torch.empty((n_steps + 1,) + tuple(X0.shape), dtype=torch.float64, device=dev),
+              torch.empty((n_steps + 1,) + tuple(X0.shape), dtype=torch.float64, device=dev))
+    for _ in range(warmup):
+        out = bt.rollout(X0, V0, A, XB, VB, states=states)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        out = bt.rollout(X0, V0, A, XB, VB, states=states)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    mstat = out[5].cpu().numpy()
+    solves = len(probs) * n_steps
+    res = {"workload": "1,024 2D bodies, tris log-uniform in [200, 8000] (total %d tris), 60 backward-Euler "
+                       "steps forward + BPTT" % bt.E,
+           "batched_ms_per_rollout": ms, "solves_per_s": solves / (ms / 1e3),
+           "bodies_failed": int((mstat[:, 0] != 0).sum()),
+           "newton_iters": int(mstat[:, 1].sum()), "cg_iters_fwd": int(mstat[:, 2].sum()),
+           "cg_iters_adj": int(mstat[:, 3].sum())}
+    bt.close()
+    # plain per-mesh FP64 path on a sample spread over the size range
+    order = np.argsort([p.n_elem for p in probs])
+    pick = order[np.linspace(0, len(order) - 1, plain_sample).astype(int)]
+    t_plain = 0.0
+    for i in pick:
+        p = probs[i]
+        sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle,
+                            density=p.density, gravity=p.gravity, k_contact=p.k_contact,
+                            contact_power=p.contact_power, dt=p.dt, precision="fp64", newton_rtol=1e-8,
+                            adjoint_rtol=1e-6, device=dev)
+        x0i = torch.from_numpy(p.X).to(dev)
+        v0i = torch.zeros_like(x0i)
+        ai = torch.from_numpy(np.ascontiguousarray(p.extra["a_seq"])).to(dev)
+        xbi = torch.zeros_like(x0i)
+        xbi[:, 0] = 1.0 / p.n_vert
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xT, vT, ck, _ = sim.rollout(x0i, v0i, ai, ckpt_every=20)
+        sim.rollout_backward(ai, ck, 20, xbi, torch.zeros_like(x0i))
+        torch.cuda.synchronize()
+        t_plain += time.perf_counter() - t0
+        sim.close()
+    # scale the sample to the batch by element count (cost grows with size)
+    frac = sum(probs[i].n_elem for i in pick) / sum(p.n_elem for p in probs)
+    plain_s_per_batch = t_plain / frac
+    res["plain_fp64_solves_per_s"] = solves / plain_s_per_batch
+    res["plain_sample"] = f"{plain_sample} bodies at evenly spaced size quantiles, scaled by element count"
+    res["speedup_vs_plain_fp64"] = res["solves_per_s"] / res["plain_fp64_solves_per_s"]
+    return res
 
 
 def measured_peaks():
@@ -314,6 +399,8 @@ def run_ours(args, rank, world, local_rank):
                      "kernel_ms_back_to_back": b2b_ms, "peak_source": peak_kind},
         "clocks": clk,
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(dev, max(1, min(args.steps, 3)), 1)
     if world == 1 and not args.no_cpu_baseline:
         max_cg = 8 if args.workload == "c5" else 40
         v, dt, nh = oracle_sample(p, max_cg)
