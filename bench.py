@@ -150,6 +150,36 @@ def run_batched(dev, steps, warmup, plain_sample=8):
     return res
 
 
+def run_dynamics(dev):
+    """Config 2: 64 x 32 grid (4,096 tris), 200 backward-Euler steps with
+    checkpoints every 20, forward + BPTT of the horizontal displacement of
+    the vertex mean w.r.t. the 8 x 200 group activations."""
+    import torch
+    import synth
+    from paper_2102_05791_gb300 import api
+    p = synth.make_config2()
+    group = torch.from_numpy(p.extra["group"].astype(np.int64)).to(dev)
+    sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle, density=p.density,
+                        gravity=p.gravity, k_contact=p.k_contact, contact_power=p.contact_power, dt=p.dt,
+                        precision="mixed", device=dev)
+    a_groups = torch.from_numpy(p.extra["a_groups"]).to(dev)
+    x0 = torch.from_numpy(p.X).to(dev)
+    a_seq = a_groups[:, group].contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xT, vT, ck, st = sim.rollout(x0, torch.zeros_like(x0), a_seq, ckpt_every=20)
+    xbT = torch.zeros_like(x0)
+    xbT[:, 0] = 1.0 / p.n_vert
+    _, _, ab, stb = sim.rollout_backward(a_seq, ck, 20, xbT, torch.zeros_like(x0))
+    g = torch.zeros_like(a_groups).index_add_(1, group, ab)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"workload": "64x32 grid (4,096 tris), 200 backward-Euler steps, checkpoints every 20, forward + BPTT",
+            "seconds": dt, "steps_per_s": 200 * 2 / dt, "newton_iters": st["newton_iters"] + stb["newton_iters"],
+            "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm())}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -232,6 +262,21 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def combine_ranks(times, counts, world, device):
+    """Whole-job numbers over ranks: the slowest rank's times (max) and the
+    summed work counts.  Returns times + counts as floats (identity at N=1)."""
+    import torch
+    vals = torch.tensor(list(times) + list(counts), dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        t = vals[:len(times)].clone()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = vals[len(times):].clone()
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        vals = torch.cat([t, c])
+    return [float(v) for v in vals.cpu()]
 
 
 # ---------------------------------------------------------------- reference arm / CPU baseline
@@ -354,14 +399,7 @@ def run_ours(args, rank, world, local_rank):
     b2b_ms, fin_ms = sim.time_hvp(50)
     tile_ms = tile_total_ms / max(tile_n, 1)
 
-    vals = torch.tensor([ms, ms_e2e, float(hvps), float(e2e_hvps)], dtype=torch.float64, device=dev)
-    if world > 1:
-        t = vals[:2].clone()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = vals[2:].clone()
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        vals = torch.cat([t, c])
-    ms, ms_e2e, hvps_all, e2e_all = [float(v) for v in vals.cpu()]
+    ms, ms_e2e, hvps_all, e2e_all = combine_ranks([ms, ms_e2e], [float(hvps), float(e2e_hvps)], world, dev)
     if rank != 0:
         return
     value = p.n_elem * hvps_all / (ms / 1000.0)
@@ -401,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_batched:
         line["batched"] = run_batched(dev, max(1, min(args.steps, 3)), 1)
+        line["dynamics"] = run_dynamics(dev)
     if world == 1 and not args.no_cpu_baseline:
         max_cg = 8 if args.workload == "c5" else 40
         v, dt, nh = oracle_sample(p, max_cg)
