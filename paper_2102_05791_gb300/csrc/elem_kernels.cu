@@ -366,7 +366,7 @@ struct HvpSmem {
 // shared memory, the per-corner forces overwrite the element fields in place
 // (the corner array needs (D+1)*D <= NF columns per element), and one thread
 // per local vertex adds its corners in fixed order.
-template <typename T, int D, bool CG, int MINB>
+template <typename T, int D, bool CG, int MINB, int MTE>
 __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
                                                   const T *__restrict__ u, const T *__restrict__ a,
                                                   const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
@@ -374,7 +374,9 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
 {
     if (CG && sc->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    const HvpSmem<T, D> L(td.max_te, td.max_tv);
+    // MTE != 0: the tile capacity is a compile-time constant, so every
+    // element-field and corner offset below folds into an immediate
+    const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
     T *sE = reinterpret_cast<T *>(smem + L.e);
     const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     const int t = blockIdx.x;
     const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
     const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
-    const int mte = td.max_te;
+    const int mte = MTE ? MTE : td.max_te;
     constexpr int NF = HvpSmem<T, D>::NF;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -712,11 +714,19 @@ int hvp_blocks_per_sm(const Ctx &c)
     return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
 
+// Tile capacities with a compile-time specialisation (the library defaults).
+constexpr int kCap2 = 512, kCap3 = 384;
+
 template <typename T, int D, bool CG, int MINB>
 static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
-    k_tile_hvp<T, D, CG, MINB><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(c.td, edev<T>(c), c.vd, ph, u, a, v, y,
-                                                                               hp, c.partials, c.sc);
+    constexpr int CAP = D == 2 ? kCap2 : kCap3;
+    if (sizeof(T) == 4 && c.td.max_te == CAP)
+        k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0)><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(
+            c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+    else
+        k_tile_hvp<T, D, CG, MINB, 0><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(c.td, edev<T>(c), c.vd, ph, u,
+                                                                                      a, v, y, hp, c.partials, c.sc);
 }
 
 template <typename T, bool CG>
@@ -804,11 +814,15 @@ cudaError_t configure_elem_kernels()
     SET((k_tile_energy<3>));
     SET((k_tile_grad<2>));
     SET((k_tile_grad<3>));
-#define SET_HVP(T, MB)                    \
-    SET((k_tile_hvp<T, 2, true, MB>));    \
-    SET((k_tile_hvp<T, 3, true, MB>));    \
-    SET((k_tile_hvp<T, 2, false, MB>));   \
-    SET((k_tile_hvp<T, 3, false, MB>));
+#define SET_HVP(T, MB)                                  \
+    SET((k_tile_hvp<T, 2, true, MB, 0>));               \
+    SET((k_tile_hvp<T, 3, true, MB, 0>));               \
+    SET((k_tile_hvp<T, 2, false, MB, 0>));              \
+    SET((k_tile_hvp<T, 3, false, MB, 0>));              \
+    SET((k_tile_hvp<T, 2, true, MB, (sizeof(T) == 4 ? kCap2 : 0)>));  \
+    SET((k_tile_hvp<T, 3, true, MB, (sizeof(T) == 4 ? kCap3 : 0)>));  \
+    SET((k_tile_hvp<T, 2, false, MB, (sizeof(T) == 4 ? kCap2 : 0)>)); \
+    SET((k_tile_hvp<T, 3, false, MB, (sizeof(T) == 4 ? kCap3 : 0)>));
     SET_HVP(float, 3)
     SET_HVP(float, 4)
     SET_HVP(double, 1)
