@@ -351,7 +351,6 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sim.set_kernel_timing(True)  # CUDA events around the HVP tile launches inside the timed solves
     clocks = Clocks(local_rank)
     hvps = 0
     launches0 = sim.kernel_launches()
@@ -371,6 +370,12 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # one more step with CUDA events around every HVP tile launch: the kernel's
+    # mean duration inside the solve (the events split the programmatic
+    # launch edges into the tile kernel, so this step is kept out of `value`)
+    sim.set_kernel_timing(True)
+    step()
+    torch.cuda.synchronize()
     tile_total_ms, tile_n = sim.kernel_timing()
     sim.set_kernel_timing(False)
     launches = sim.kernel_launches() - launches0
@@ -434,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
                      "kernel": "k_tile_hvp<float,3>", "kernel_ms": tile_ms, "kernel_launches_timed": tile_n,
+                     "kernel_timing": "CUDA event nodes around every tile launch in one profiled solve after the timed steps",
                      "kernel_ms_back_to_back": b2b_ms, "peak_source": peak_kind},
         "clocks": clk,
     }

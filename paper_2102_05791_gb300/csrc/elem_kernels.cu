@@ -26,6 +26,7 @@
 #include "reduce.cuh"
 #include "tma.cuh"
 #include "elem_math.cuh"
+#include "pdl.cuh"
 
 namespace softsim {
 
@@ -372,7 +373,6 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
                                                   const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
                                                   double *__restrict__ partials, DevScalars *__restrict__ sc)
 {
-    if (CG && sc->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     // MTE != 0: the tile capacity is a compile-time constant, so every
     // element-field and corner offset below folds into an immediate
@@ -410,6 +410,16 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         bulk_g2s_stream(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1, pol);
     }
     __syncthreads();
+    // Everything copied so far is static during a solve; state (u, v) and the
+    // CG scalars are read only after the predecessor kernel has completed.
+    pdl_wait();
+    if (CG && sc->done) {  // CG already finished: drain the copies, then leave
+        if (threadIdx.x == 0) {
+            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar + 1, 0);
+        }
+        return;
+    }
     // every thread takes the same decision, so no thread is left at a barrier
     if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
         if (threadIdx.x == 0) {
@@ -537,6 +547,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             dot += vt;
         }
     }
+    pdl_trigger();  // the alpha reduction may be scheduled once every tile is done
     if (CG) {
         const double s = block_sum(dot);
         if (threadIdx.x == 0) partials[t] = s;  // reduced by k_cg_alpha
@@ -722,11 +733,11 @@ static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *a, con
 {
     constexpr int CAP = D == 2 ? kCap2 : kCap3;
     if (sizeof(T) == 4 && c.td.max_te == CAP)
-        k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0)><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(
-            c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0)>, dim3(c.td.n_tiles), dim3(c.threads),
+                 hvp_smem<T>(c), s, c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
     else
-        k_tile_hvp<T, D, CG, MINB, 0><<<c.td.n_tiles, c.threads, hvp_smem<T>(c), s>>>(c.td, edev<T>(c), c.vd, ph, u,
-                                                                                      a, v, y, hp, c.partials, c.sc);
+        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s, c.td,
+                 edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
 }
 
 template <typename T, bool CG>

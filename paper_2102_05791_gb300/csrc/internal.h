@@ -117,6 +117,7 @@ struct Ctx {
     int n_fin_blocks = 1;
     DevScalars *sc = nullptr;
     mutable int64_t n_launch = 0;  // kernels launched through this context
+    mutable bool pdl = false;      // launch CG-loop kernels with programmatic dependent launch
 };
 
 // ---------------------------------------------------------------- launchers

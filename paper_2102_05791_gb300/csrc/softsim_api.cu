@@ -471,6 +471,7 @@ template <typename T>
 static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
 {
     T *d = (T *)h->vd, *r = (T *)h->vr, *p = (T *)h->vp, *Ap = (T *)h->vAp;
+    h->ctx.pdl = true;  // programmatic edges between the kernels of the captured block
     for (int k = 0; k < kCgBlock; ++k) {
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
         launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), View<T>::a(h), p, Ap, View<T>::hp(h), s);
@@ -478,6 +479,7 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
         launch_cg_update_halo<T>(h->ctx, ph, View<T>::u(h), d, r, p, Ap, View<T>::hp(h), s);
         launch_cg_dir<T>(h->ctx, p, r, s);
     }
+    h->ctx.pdl = false;
 }
 
 template <typename T>

@@ -9,6 +9,7 @@
 // reductions.  Vectors are float (mixed precision) or double.
 #include "internal.h"
 #include "reduce.cuh"
+#include "pdl.cuh"
 
 namespace softsim {
 
@@ -94,6 +95,8 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
                                                         const T *__restrict__ Ap, const T *__restrict__ hp,
                                                         double *__restrict__ partials, DevScalars *sc)
 {
+    pdl_trigger();
+    pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
     const bool neg = sc->negcurv != 0;
     const bool first = sc->iter == 0;
@@ -149,6 +152,8 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
 // One block: p.Ap from the HVP tile partials -> alpha (or non-positive curvature).
 __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ partials, int n, DevScalars *sc)
 {
+    pdl_trigger();
+    pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
     const double pAp = sum_partials(partials, n);
     if (threadIdx.x == 0) {
@@ -165,6 +170,8 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ pa
 // One block: r.r from the update partials -> beta, iteration count, done.
 __global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ partials, int n, DevScalars *sc)
 {
+    pdl_trigger();
+    pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
     const double tot = sum_partials(partials, n);
     if (threadIdx.x == 0) {
@@ -183,6 +190,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, const T *__restrict__ r,
                                                 const DevScalars *sc)
 {
+    pdl_trigger();
+    pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
     const T beta = T(sc->beta);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -376,16 +385,18 @@ void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r,
     c.n_launch += 2;
     const int g = vec_grid(c.nv * 4);
     if (c.dim == 2)
-        k_cg_update_halo<T, 2><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
+        launch_k(c.pdl, k_cg_update_halo<T, 2>, dim3(g), dim3(256), 0, s, c.td, c.vd, ph, u, d, r, p, Ap, hp,
+                 c.partials, c.sc);
     else
-        k_cg_update_halo<T, 3><<<g, 256, 0, s>>>(c.td, c.vd, ph, u, d, r, p, Ap, hp, c.partials, c.sc);
-    k_cg_beta<<<1, 1024, 0, s>>>(c.partials, g, c.sc);
+        launch_k(c.pdl, k_cg_update_halo<T, 3>, dim3(g), dim3(256), 0, s, c.td, c.vd, ph, u, d, r, p, Ap, hp,
+                 c.partials, c.sc);
+    launch_k(c.pdl, k_cg_beta, dim3(1), dim3(1024), 0, s, (const double *)c.partials, g, c.sc);
 }
 
 void launch_cg_alpha(const Ctx &c, int n_partials, cudaStream_t s)
 {
     c.n_launch += 1;
-    k_cg_alpha<<<1, 1024, 0, s>>>(c.partials, n_partials, c.sc);
+    launch_k(c.pdl, k_cg_alpha, dim3(1), dim3(1024), 0, s, (const double *)c.partials, n_partials, c.sc);
 }
 
 template <typename T>
@@ -393,7 +404,7 @@ void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s)
 {
     c.n_launch += 1;
     const int64_t n = c.nv * c.dim;
-    k_cg_dir<T><<<vec_grid(n), 256, 0, s>>>(n, p, r, c.sc);
+    launch_k(c.pdl, k_cg_dir<T>, dim3(vec_grid(n)), dim3(256), 0, s, n, p, (const T *)r, (const DevScalars *)c.sc);
 }
 
 template <typename T>
