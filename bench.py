@@ -330,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     p, desc = workload(args.workload)
     sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle, density=p.density,
-                        gravity=p.gravity, precision=args.precision, device=dev)
+                        gravity=p.gravity, precision=args.precision, tile_elems="auto", device=dev)
     a = torch.from_numpy(p.a).to(dev)
     tgt = torch.from_numpy(p.target).to(dev)
     n = p.n_vert
@@ -426,6 +426,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32 HVP/CG vectors, f64 state+gradient+energy+reductions" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision,
+                   "tile_shape": {"elems_per_tile": sim.tile_shape[0], "threads": sim.tile_shape[1],
+                                  "picked_by": "paper_2102_05791_gb300.autotune"},
                    "l2": f"inputs larger than L2: {(BYTES_PER_TET * p.n_elem) / 1e6:.0f} MB element data per HVP"},
         "solves_per_s": world * args.steps / (ms / 1000.0),
         "hvp_per_step": hvps_all / args.steps / world,

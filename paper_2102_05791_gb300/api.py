@@ -40,6 +40,8 @@ class Simulator:
 
     Arguments mirror ``sim_mesh`` / ``sim_material`` / ``sim_options`` in
     include/softsim.h.  Host arrays (numpy or CPU tensors) are copied.
+    ``tile_elems="auto"`` (or ``threads="auto"``) picks the tile shape with
+    the autotuner (paper_2102_05791_gb300.autotune, cached per GPU).
     """
 
     def __init__(self, X, T, fixed=None, fiber=None, *, mu, lam, k_muscle=0.0, density=0.0, gravity=0.0,
@@ -48,6 +50,13 @@ class Simulator:
                  threads=0, device=None):
         self._lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if tile_elems == "auto" or threads == "auto":
+            from . import autotune
+            with torch.cuda.device(self.device):
+                tile_elems, threads = autotune.best_tile_shape(
+                    X, T, fixed, fiber, precision=precision, mu=mu, lam=lam, k_muscle=k_muscle, density=density,
+                    gravity=gravity, k_contact=k_contact, contact_power=contact_power, log_mode=log_mode, dt=dt)
+        self.tile_shape = (int(tile_elems), int(threads))
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
         T = np.ascontiguousarray(np.asarray(T, dtype=np.int32))
         self.dim = int(X.shape[1])

@@ -1,0 +1,102 @@
+"""Autotuner for the tile shape of the HVP kernel.
+
+For a mesh, tries candidate (elements per tile, threads per block) pairs:
+builds a handle for each, runs a short adjoint CG solve at the rest shape
+with in-solve kernel timing (CUDA events around every HVP tile launch inside
+the captured CG graph), and keeps the pair with the smallest mean launch
+time.  Results are cached in a JSON file keyed by GPU name, dimension,
+element-count bucket (power of two) and precision, so later handles of a
+similar mesh reuse the choice without tuning.
+
+    from paper_2102_05791_gb300 import autotune
+    te, th = autotune.best_tile_shape(X, T, fixed, fiber, mu=..., lam=..., ...)
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+CANDIDATES = {
+    3: [(384, 128), (384, 256), (256, 128), (512, 128), (512, 256), (768, 256)],
+    2: [(512, 256), (512, 128), (384, 128), (768, 256), (1024, 256)],
+}
+
+
+def cache_path() -> str:
+    return os.environ.get("SOFTSIM_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "softsim", "autotune.json"))
+
+
+def _key(dim: int, n_elem: int, precision: str) -> str:
+    import torch
+    name = torch.cuda.get_device_name(torch.cuda.current_device())
+    bucket = int(math.log2(max(n_elem, 1)))
+    return f"{name}|d{dim}|e2^{bucket}|{precision}"
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(cache: dict) -> None:
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def measure(X, T, fixed, fiber, tile_elems: int, threads: int, precision: str = "mixed", iters: int = 48,
+            **material) -> float:
+    """Mean in-solve HVP tile-kernel time (ms) for one tile shape."""
+    import torch
+
+    from . import api
+    sim = api.Simulator(X, T, fixed, fiber, precision=precision, tile_elems=tile_elems, threads=threads,
+                        max_adjoint_cg=iters, adjoint_rtol=1e-30, **material)
+    try:
+        dev = sim.device
+        x = sim.X
+        a = torch.zeros(sim.n_elem, dtype=torch.float64, device=dev)
+        rng = np.random.default_rng(0)
+        b = torch.from_numpy(rng.standard_normal((sim.n_vert, sim.dim))).to(dev)
+        sim.adjoint(x, a, b, check=False)  # warm-up: graph capture, module loading
+        sim.set_kernel_timing(True)
+        sim.adjoint(x, a, b, check=False)
+        torch.cuda.synchronize()
+        ms, n = sim.kernel_timing()
+        sim.set_kernel_timing(False)
+        return ms / max(n, 1)
+    finally:
+        sim.close()
+
+
+def best_tile_shape(X, T, fixed=None, fiber=None, precision: str = "mixed", candidates=None, use_cache: bool = True,
+                    **material):
+    """(tile_elems, threads) with the fastest HVP tile kernel for this mesh."""
+    X = np.asarray(X)
+    T = np.asarray(T)
+    dim = X.shape[1]
+    key = _key(dim, len(T), precision)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key]["best"])
+    times = {}
+    for te, th in (candidates or CANDIDATES[dim]):
+        try:
+            times[(te, th)] = measure(X, T, fixed, fiber, te, th, precision, **material)
+        except Exception:  # a shape this mesh cannot use (e.g. too few threads for a tile)
+            times[(te, th)] = float("inf")
+    best = min(times, key=times.get)
+    if use_cache:
+        cache[key] = {"best": list(best), "ms": {f"{k[0]}x{k[1]}": v for k, v in times.items()}}
+        _store(cache)
+    return best
