@@ -49,6 +49,7 @@ class _Model(C.Structure):
         ("gravity", C.c_double), ("k_contact", C.c_double),
         ("contact_power", C.c_int), ("log_mode", C.c_int),
         ("h", C.c_double), ("xhat", C.c_void_p),
+        ("k_friction", C.c_double), ("eps_friction", C.c_double), ("x0", C.c_void_p),
     ]
 
 
@@ -113,6 +114,9 @@ class Model:
     log_mode: int
     h: float = 0.0
     xhat: np.ndarray | None = None
+    k_friction: float = 0.0
+    eps_friction: float = 0.01
+    x0: np.ndarray | None = None
 
     @property
     def nv(self):
@@ -136,6 +140,8 @@ class Model:
         m.contact_power, m.log_mode = int(self.contact_power), int(self.log_mode)
         m.h = self.h
         m.xhat = _p(self.xhat)
+        m.k_friction, m.eps_friction = self.k_friction, self.eps_friction
+        m.x0 = _p(self.x0)
         return m
 
     # -- element-level maps -------------------------------------------------
@@ -233,7 +239,9 @@ def make_model(prob, log_mode=None, with_fixed=True, h=None, xhat=None) -> Model
                  gravity=float(prob.gravity), k_contact=float(prob.k_contact),
                  contact_power=int(prob.contact_power),
                  log_mode=int(prob.log_mode if log_mode is None else log_mode),
-                 h=float(prob.dt if h is None else h), xhat=None if xhat is None else _f64(xhat))
+                 h=float(prob.dt if h is None else h), xhat=None if xhat is None else _f64(xhat),
+                 k_friction=float(getattr(prob, "k_friction", 0.0)),
+                 eps_friction=float(getattr(prob, "eps_friction", 0.01)))
 
 
 # ---------------------------------------------------------------------------
@@ -266,7 +274,7 @@ def be_step(model: Model, x0, v0, a, rtol=1e-8, max_newton=100):
     """x1 = argmin 1/2 |x - (x0 + h v0)|_M^2 + h^2 E(x, a); v1 = (x1 - x0)/h."""
     h = model.h
     xhat = _f64(x0 + h * v0)
-    m = model.replace(xhat=xhat)
+    m = model.replace(xhat=xhat, x0=_f64(x0))
     x1, st = m.newton(a, x_init=x0, rtol=rtol, max_newton=max_newton)
     v1 = (x1 - x0) / h
     return x1, v1, st
@@ -282,11 +290,22 @@ def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12):
       abar  = -h^2 lambda^T d2E/dx da.
     """
     h = model.h
-    m = model.replace(xhat=_f64(x0 + h * v0))
+    m = model.replace(xhat=_f64(x0 + h * v0), x0=_f64(x0))
     b = xbar1 + vbar1 / h
     lam, it = m.adjoint(x1, a, b, rtol=adj_rtol)
     Ml = model.mass[:, None] * lam
     xbar0 = Ml - vbar1 / h
+    if model.k_friction != 0.0:
+        # friction depends on x0: h^2 grad_x E_f = fw (x - x0) on horizontal axes,
+        # fw = 2 k_f ReLU(eps - y0); xbar0 -= lambda^T d(that)/dx0
+        y0 = x0[:, 1]
+        active = (model.eps_friction - y0) > 0.0
+        fw = 2.0 * model.k_friction * np.where(active, model.eps_friction - y0, 0.0)
+        for c in range(x0.shape[1]):
+            if c == 1:
+                continue
+            xbar0[:, c] += fw * lam[:, c]
+            xbar0[:, 1] += 2.0 * model.k_friction * active * lam[:, c] * (x1[:, c] - x0[:, c])
     vbar0 = h * Ml
     if model.fixed is not None:
         fx = model.fixed.astype(bool)

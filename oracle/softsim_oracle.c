@@ -15,7 +15,9 @@
  *   - the Hessian-vector product that the paper obtains by back-propagating
  *     <f, v> (Eq. matrix-free-dfdx, Sec. 3.1), written out analytically;
  *   - the parameter VJP -lambda^T d2E/dx da (Eq. dLda-re-ordered, Sec. 3);
- *   - the backward-Euler incremental potential (Eq. opt-be, Sec. 4);
+ *   - the backward-Euler incremental potential (Eq. opt-be, Sec. 4), with
+ *     the optional ground friction k_f |v_horizontal|^2 ReLU(eps - y0) of
+ *     Sec. 4.2 evaluated at v = (x - x0)/h;
  *   - the energy minimisation of Eq. x1-quasistatic-argmin by Newton-CG with
  *     backtracking, and a CG solve for the adjoint system (Sec. 3).
  *
@@ -44,6 +46,9 @@ typedef struct {
     int log_mode;               /* 0 exact log J, 1 quadratic q(J) */
     double h;                   /* time step; 0 = quasistatic */
     const double *xhat;         /* [nv][d] inertial target x0 + h v0 (dynamics only) */
+    double k_friction;          /* ground friction stiffness (dynamics only; 0 = off) */
+    double eps_friction;        /* contact tolerance of the friction weight */
+    const double *x0;           /* [nv][d] previous positions (dynamics only) */
 } or_model;
 
 typedef struct {
@@ -205,6 +210,17 @@ void or_mass(int d, long nv, long ne, const int *T, const double *W, double rho,
 
 /* ---------------------------------------------------------------- energy */
 
+/* Ground friction (Sec. 4.2, Eq. energy-friction): with the velocity
+ * v(x) = (x - x0)/h of backward Euler (Eq. v-of-x-vec), each vertex adds
+ * k_f |v_horizontal(x)|^2 ReLU(eps - y0), horizontal meaning every axis but
+ * y (x in 2D; x and z in 3D).  Weight of vertex i: */
+static double friction_w(const or_model *M, long i)
+{
+    if (!(M->h > 0.0) || !M->x0 || M->k_friction == 0.0) return 0.0;
+    double r = M->eps_friction - M->x0[i * M->d + 1];
+    return r > 0.0 ? M->k_friction * r : 0.0;
+}
+
 /* Per-vertex ground penalty k_c * max(0, -y)^p and its first two derivatives. */
 static double contact_e(const or_model *M, double y)
 {
@@ -270,6 +286,13 @@ double or_energy(const or_model *M, const double *x, const double *a, double *ab
         double y = x[i * d + 1];
         double m = M->mass ? M->mass[i] : 0.0;
         double t = m * M->gravity * y + contact_e(M, y);
+        double w = friction_w(M, i);
+        if (w != 0.0)
+            for (int c = 0; c < d; ++c) {
+                if (c == 1) continue;
+                double vc = (x[i * d + c] - M->x0[i * d + c]) / M->h;
+                t += w * vc * vc;
+            }
         E += t;
         S += fabs(t);
     }
@@ -361,6 +384,14 @@ void or_grad(const or_model *M, const double *x, const double *a, double *g, dou
         double m = M->mass ? M->mass[i] : 0.0;
         g[i * d + 1] += m * M->gravity + contact_de(M, y);
         if (abs_scale) abs_scale[i * d + 1] += fabs(m * M->gravity) + fabs(contact_de(M, y));
+        double w = friction_w(M, i);
+        if (w != 0.0)
+            for (int c = 0; c < d; ++c) {
+                if (c == 1) continue;
+                double gf = 2.0 * w * (x[i * d + c] - M->x0[i * d + c]) / (M->h * M->h);
+                g[i * d + c] += gf;
+                if (abs_scale) abs_scale[i * d + c] += fabs(gf);
+            }
     }
     if (M->h > 0.0) {
         double h2 = M->h * M->h;
@@ -453,7 +484,13 @@ void or_hvp(const or_model *M, const double *x, const double *a, const double *v
             for (int j = 0; j < d; ++j) G[i][j] *= M->W[e];
         scatter(M, e, G, Hv);
     }
-    for (long i = 0; i < M->nv; ++i) Hv[i * d + 1] += contact_d2e(M, x[i * d + 1]) * v[i * d + 1];
+    for (long i = 0; i < M->nv; ++i) {
+        Hv[i * d + 1] += contact_d2e(M, x[i * d + 1]) * v[i * d + 1];
+        double w = friction_w(M, i);
+        if (w != 0.0)
+            for (int c = 0; c < d; ++c)
+                if (c != 1) Hv[i * d + c] += 2.0 * w / (M->h * M->h) * v[i * d + c];
+    }
     if (M->h > 0.0) {
         double h2 = M->h * M->h;
         for (long i = 0; i < M->nv; ++i)
