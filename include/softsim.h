@@ -76,7 +76,12 @@ typedef struct {
  *   l(J) = (J-1) - (J-1)^2/2 (SIM_LOG_QUAD, the quadratic stand-in of Sec. 2),
  *   W_e the rest area / volume, m_i = sum over elements of rho W_e/(dim+1).
  * dt > 0 selects backward Euler (Eq. opt-be): the solver then minimises
- *   1/2 |x - (x0 + dt v0)|_M^2 + dt^2 E(x, a). */
+ *   1/2 |x - (x0 + dt v0)|_M^2 + dt^2 E(x, a).
+ * k_friction > 0 (dynamics only; ignored when dt == 0) adds the ground
+ * friction of Sec. 4.2, dt^2 sum_i k_f |v_h,i|^2 ReLU(eps_friction - y0_i),
+ * with v = (x - x0)/dt and v_h its horizontal part (every axis but y): the
+ * damping acts on vertices that started the step within eps_friction of
+ * the ground (or below it).  A zero-initialised struct has friction off. */
 typedef struct {
     double mu, lambda;        /* Lame parameters */
     double k_muscle;          /* muscle stiffness k */
@@ -87,6 +92,8 @@ typedef struct {
     int log_mode;             /* SIM_LOG_EXACT or SIM_LOG_QUAD */
     double dt;                /* 0 = quasistatic; > 0 = backward-Euler step */
     const double *fiber;      /* HOST [n_elem][dim] unit fiber directions */
+    double k_friction;        /* ground friction stiffness k_f (0 = off) */
+    double eps_friction;      /* height below which friction acts */
 } sim_material;
 
 typedef struct {
@@ -162,7 +169,9 @@ int sim_newton_solve(sim_handle *h, const double *x_init, const double *a, const
 
 /* Adjoint solve at a converged state (Eq. dLda-re-ordered): lambda =
  * A^-1 b with A = H(x*, a) (quasistatic) or M + dt^2 H(x*, a) (backward
- * Euler), b = dLdx with pinned entries dropped; CG to adjoint_rtol. */
+ * Euler), b = dLdx with pinned entries dropped; CG to adjoint_rtol.  With
+ * friction, A uses the friction weights of the last step prepared by
+ * sim_newton_solve / sim_step_forward / sim_step_backward. */
 int sim_adjoint_solve(sim_handle *h, const double *x_star, const double *a, const double *dLdx,
                       double *lambda, sim_solve_stats *stats, void *stream);
 
@@ -183,6 +192,10 @@ int sim_step_forward(sim_handle *h, const double *x0, const double *v0, const do
  *   lambda = (M + dt^2 H(x1))^-1 (xbar1 + vbar1/dt),
  *   xbar0 = M lambda - vbar1/dt,  vbar0 = dt M lambda,
  *   abar = -dt^2 lambda^T d2E/dx da.
+ * With friction, H includes its horizontal stiffness fw_i = 2 k_f ReLU(eps -
+ * y0_i) and xbar0 gains fw_i lambda_h,i on the horizontal axes and
+ * 2 k_f [y0_i < eps] lambda_h,i . (x1 - x0)_h,i on y; x0 is then required
+ * (v0 is never read).
  * Outputs may not alias inputs; xbar0/vbar0 are zero at pinned vertices. */
 int sim_step_backward(sim_handle *h, const double *x0, const double *v0, const double *x1,
                       const double *a, const double *xbar1, const double *vbar1, double *xbar0,
@@ -233,9 +246,9 @@ int sim_tile_stats(const sim_handle *h, int *n_tiles, double *elems_per_tile,
                    double *verts_per_tile, double *halo_fraction);
 
 /* ---------------------------------------------------------------- batches
- * Many independent meshes of uneven size (same dim; materials may differ
- * only in mu and lambda), each rolled out for n_steps backward-Euler steps
- * (Eq. opt-be) and differentiated by backpropagation through time, in ONE
+ * Many independent meshes of uneven size (same dim; materials, ground
+ * friction included, may differ only in mu and lambda), each rolled out for
+ * n_steps backward-Euler steps (Eq. opt-be) and differentiated by backpropagation through time, in ONE
  * persistent kernel launch replayed from a captured CUDA graph.  Each CTA
  * takes the next mesh (largest first) and runs its whole forward rollout
  * (Newton-CG per step) and backward pass (refined adjoint CG and parameter

@@ -38,7 +38,7 @@ class SimMaterial(C.Structure):
     _fields_ = [("mu", C.c_double), ("lambda_", C.c_double), ("k_muscle", C.c_double),
                 ("density", C.c_double), ("gravity", C.c_double), ("k_contact", C.c_double),
                 ("contact_power", C.c_int), ("log_mode", C.c_int), ("dt", C.c_double),
-                ("fiber", C.c_void_p)]
+                ("fiber", C.c_void_p), ("k_friction", C.c_double), ("eps_friction", C.c_double)]
 
 
 class SimOptions(C.Structure):

@@ -45,7 +45,8 @@ class Simulator:
     """
 
     def __init__(self, X, T, fixed=None, fiber=None, *, mu, lam, k_muscle=0.0, density=0.0, gravity=0.0,
-                 k_contact=0.0, contact_power=3, log_mode=0, dt=0.0, precision="mixed", newton_rtol=1e-8, newton_forcing=0.5,
+                 k_contact=0.0, contact_power=3, log_mode=0, dt=0.0, k_friction=0.0, eps_friction=0.01,
+                 precision="mixed", newton_rtol=1e-8, newton_forcing=0.5,
                  adjoint_rtol=1e-6, max_newton=100, max_cg=500, max_adjoint_cg=0, max_ls=30, tile_elems=0,
                  threads=0, device=None):
         self._lib = L.load()
@@ -68,7 +69,7 @@ class Simulator:
                          None if fx is None else fx.ctypes.data)
         mat = L.SimMaterial(float(mu), float(lam), float(k_muscle), float(density), float(gravity),
                             float(k_contact), int(contact_power), int(log_mode), float(dt),
-                            None if fb is None else fb.ctypes.data)
+                            None if fb is None else fb.ctypes.data, float(k_friction), float(eps_friction))
         opt = L.SimOptions()
         self._lib.sim_default_options(C.byref(opt))
         opt.precision = L.SIM_PREC_MIXED if precision == "mixed" else L.SIM_PREC_FP64
@@ -268,7 +269,8 @@ class Batch:
             self._keep += [X, T, fx, fb]
             meshes[i] = L.SimMesh(X.shape[1], X.shape[0], T.shape[0], X.ctypes.data, T.ctypes.data, fx.ctypes.data)
             mats[i] = L.SimMaterial(p.mu, p.lam, p.k_muscle, p.density, p.gravity, p.k_contact, p.contact_power,
-                                    p.log_mode, p.dt, fb.ctypes.data)
+                                    p.log_mode, p.dt, fb.ctypes.data, float(getattr(p, "k_friction", 0.0)),
+                                    float(getattr(p, "eps_friction", 0.01)))
         opt = L.SimOptions()
         self._lib.sim_default_options(C.byref(opt))
         opt.newton_rtol, opt.adjoint_rtol = float(newton_rtol), float(adjoint_rtol)

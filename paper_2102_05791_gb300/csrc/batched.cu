@@ -48,12 +48,14 @@ struct BatchDev {
     int64_t estride = 0;
     const double *mu = nullptr, *lam = nullptr;      // [M]
     double k = 0, grav = 0, kc = 0, dt = 0;
+    double kf = 0, feps = 0;  // ground friction k_f and its height; kf == 0: off
     int cpow = 3, log_mode = 0;
     double newton_rtol = 1e-8, adj_rtol = 1e-6;
     int max_newton = 100, max_cg = 500, max_adj_cg = 2000, max_ls = 30;
     // workspace [V][d]
     double *u = nullptr, *uhat = nullptr, *g = nullptr, *w64 = nullptr, *r64 = nullptr, *Hx = nullptr,
            *lacc = nullptr, *xbar = nullptr, *vbar = nullptr;
+    double *fw = nullptr, *u0 = nullptr;  // friction: [V] 2 k_f ReLU(eps - y0), [V][d] x0 - X (kf > 0 only)
     float *u32 = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
     float *c32 = nullptr;   // corners [E*(d+1)][d]
     double *c64 = nullptr;
@@ -209,6 +211,12 @@ __device__ double grad_pass(const BatchDev &b, const Mesh &m, const double *a_t,
         acc[1] += s_el * (mass * b.grav + contact_d1(y, b.kc, b.cpow));
 #pragma unroll
         for (int q = 0; q < D; ++q) acc[q] += mass * (b.u[v * D + q] - b.uhat[v * D + q]);
+        if (b.fw) {
+            const double fv = b.fw[v];
+#pragma unroll
+            for (int q = 0; q < D; ++q)
+                if (q != 1) acc[q] += fv * (b.u[v * D + q] - b.u0[v * D + q]);
+        }
         const bool fx = b.fixed[v] != 0;
 #pragma unroll
         for (int q = 0; q < D; ++q) {
@@ -277,6 +285,10 @@ __device__ double energy_pass(const BatchDev &b, const Mesh &m, const double *a_
             const double rq = uq - b.uhat[v * D + q];
             in += 0.5 * mass * rq * rq;
             if (q == 1) yv = b.X[v * D + 1] + uq;
+            else if (b.fw) {
+                const double rf = uq - b.u0[v * D + q];
+                in += 0.5 * b.fw[v] * rf * rf;
+            }
         }
         const double pen = yv < 0.0 ? -yv : 0.0;
         const double w = s_el * (mass * b.grav * yv + b.kc * (b.cpow == 2 ? pen * pen : pen * pen * pen));
@@ -360,9 +372,10 @@ __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, 
 #pragma unroll
         for (int q = 0; q < D; ++q) vv[q] = fx ? T(0) : v[vg * D + q];
         acc[1] += T(b.dt * b.dt * contact_d2(yy, b.kc, b.cpow)) * vv[1];
+        const T mh = b.fw ? mass + T(b.fw[vg]) : mass;  // friction stiffens the horizontal axes
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-            const T o = fx ? T(0) : acc[q] + mass * vv[q];
+            const T o = fx ? T(0) : acc[q] + (q == 1 ? mass : mh) * vv[q];
             y[vg * D + q] = o;
             dot += (double)vv[q] * (double)o;
         }
@@ -418,6 +431,20 @@ __device__ __forceinline__ void set_u32(const BatchDev &b, int64_t o, int64_t n)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.u32[o + i] = (float)b.u[o + i];
 }
 
+// Friction data of a step of mesh m started at x0: u0 = x0 - X and
+// fw = 2 k_f ReLU(eps - y0) per vertex.
+template <int D>
+__device__ void friction_prep(const BatchDev &b, const Mesh &m, const double *x0)
+{
+    for (int lv = threadIdx.x; lv < m.nv; lv += blockDim.x) {
+        const int64_t v = m.v0 + lv;
+#pragma unroll
+        for (int q = 0; q < D; ++q) b.u0[v * D + q] = x0[v * D + q] - b.X[v * D + q];
+        const double r = b.feps - x0[v * D + 1];
+        b.fw[v] = r > 0.0 ? 2.0 * b.kf * r : 0.0;
+    }
+}
+
 // Backward-Euler step of mesh m: x1 = argmin of the incremental potential,
 // started from x0; returns the step's status and adds iteration counts.
 template <int D>
@@ -429,6 +456,7 @@ __device__ int step_forward(const BatchDev &b, const Mesh &m, const double *x0, 
         b.u[o + i] = b.fixed[m.v0 + i / D] ? 0.0 : x0[o + i] - b.X[o + i];
         b.uhat[o + i] = x0[o + i] + b.dt * v0[o + i] - b.X[o + i];
     }
+    if (b.fw) friction_prep<D>(b, m, x0);
     __syncthreads();
     double S0;
     double gn = sqrt(grad_pass<D>(b, m, a_t, red));
@@ -493,11 +521,12 @@ __device__ int step_forward(const BatchDev &b, const Mesh &m, const double *x0, 
 // (xbar + vbar/h) with FP64 refinement, then xbar <- M lambda - vbar/h,
 // vbar <- h M lambda, abar_t = -h^2 lambda^T d2E/dx da.
 template <int D>
-__device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x1, const double *a_t, double *abar_t,
-                             int *cg_it, double *red)
+__device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0, const double *x1, const double *a_t,
+                             double *abar_t, int *cg_it, double *red)
 {
     const int64_t o = m.v0 * D, n = (int64_t)m.nv * D;
     const double h = b.dt;
+    if (b.fw) friction_prep<D>(b, m, x0);
     double bn = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         b.u[o + i] = x1[o + i] - b.X[o + i];
@@ -543,14 +572,28 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x1,
         rn = rnew;
     }
     if (rn <= b.adj_rtol * bn) status = SIM_OK;
-    // xbar0 = M lambda - vbar1/h, vbar0 = h M lambda
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t v = m.v0 + i / D;
-        const double ml = b.mass[v] * b.lacc[o + i];
+    // xbar0 = M lambda - vbar1/h, vbar0 = h M lambda; with friction, plus
+    // fw lambda_h on the horizontal axes and 2 k_f [y0 < eps] lambda_h . (x1 - x0)_h on y
+    for (int lv = threadIdx.x; lv < m.nv; lv += blockDim.x) {
+        const int64_t v = m.v0 + lv;
         const bool fx = b.fixed[v] != 0;
-        const double vb = b.vbar[o + i];
-        b.xbar[o + i] = fx ? 0.0 : ml - vb / h;
-        b.vbar[o + i] = fx ? 0.0 : h * ml;
+        const double fv = b.fw ? b.fw[v] : 0.0;
+        double ysum = 0.0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const int64_t i = v * D + q;
+            const double l = b.lacc[i];
+            const double ml = b.mass[v] * l;
+            const double vb = b.vbar[i];
+            double xb = ml - vb / h;
+            if (q != 1 && fv > 0.0) {
+                xb += fv * l;
+                ysum += l * (x1[i] - x0[i]);
+            }
+            b.xbar[i] = fx ? 0.0 : xb;
+            b.vbar[i] = fx ? 0.0 : h * ml;
+        }
+        if (fv > 0.0 && !fx) b.xbar[v * D + 1] += 2.0 * b.kf * ysum;
     }
     // parameter VJP at x1
     for (int le = threadIdx.x; le < m.ne; le += blockDim.x) {
@@ -615,8 +658,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
         }
         __syncthreads();
         for (int t = n_steps - 1; t >= 0; --t) {
-            const int st = step_backward<D>(b, m, xs + (t + 1) * VD, a_seq + (size_t)t * E, abar_seq + (size_t)t * E,
-                                            &cg_a, red);
+            const int st = step_backward<D>(b, m, xs + t * VD, xs + (t + 1) * VD, a_seq + (size_t)t * E,
+                                            abar_seq + (size_t)t * E, &cg_a, red);
             if (st != SIM_OK && status == SIM_OK) status = st;
         }
         if (threadIdx.x == 0) {
@@ -726,8 +769,11 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     for (int m = 1; m < M; ++m)
         if (mats[m].k_muscle != m0.k_muscle || mats[m].gravity != m0.gravity || mats[m].k_contact != m0.k_contact ||
             mats[m].contact_power != m0.contact_power || mats[m].log_mode != m0.log_mode || mats[m].dt != m0.dt ||
-            mats[m].density != m0.density)
+            mats[m].density != m0.density || mats[m].k_friction != m0.k_friction ||
+            mats[m].eps_friction != m0.eps_friction)
             return bfail(bt, SIM_EINVAL, "batched meshes may differ only in mu and lambda");
+    if (!(m0.k_friction >= 0.0) || !std::isfinite(m0.k_friction) || !std::isfinite(m0.eps_friction))
+        return bfail(bt, SIM_EINVAL, "k_friction must be finite and >= 0, eps_friction finite");
     if (m0.contact_power != 2 && m0.contact_power != 3) return bfail(bt, SIM_EINVAL, "contact_power must be 2 or 3");
     const int64_t V = bt->voff[M], E = bt->eoff[M];
     bt->V = V;
@@ -827,6 +873,8 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.grav = m0.gravity;
     b.kc = m0.k_contact;
     b.dt = m0.dt;
+    b.kf = m0.k_friction;
+    b.feps = m0.eps_friction;
     b.cpow = m0.contact_power;
     b.log_mode = m0.log_mode;
     b.newton_rtol = o.newton_rtol;
@@ -845,6 +893,10 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.lacc = balloc<double>(bt, VD);
     b.xbar = balloc<double>(bt, VD);
     b.vbar = balloc<double>(bt, VD);
+    if (b.kf > 0.0) {
+        b.fw = balloc<double>(bt, V);
+        b.u0 = balloc<double>(bt, VD);
+    }
     b.u32 = balloc<float>(bt, VD);
     b.d = balloc<float>(bt, VD);
     b.r = balloc<float>(bt, VD);
@@ -859,6 +911,7 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
                           b.d, b.r, b.p, b.Ap, b.c32, b.c64, b.counter, b.mstat};
     for (const void *p : ptrs)
         if (!p) return bfail(bt, SIM_ENOMEM, "device allocation or upload failed");
+    if (b.kf > 0.0 && (!b.fw || !b.u0)) return bfail(bt, SIM_ENOMEM, "device allocation failed");
     return SIM_OK;
 }
 

@@ -170,6 +170,15 @@ __global__ void __launch_bounds__(256) k_tile_energy(TileDev td, ElemDev<double>
                     const double r = su[k * D + c] + tj * sd[k * D + c] - uhat[gid * D + c];
                     in += 0.5 * m * r * r;
                 }
+                if (ph.fw) {
+                    const double f = ph.fw[gid];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        if (c == 1) continue;
+                        const double r = su[k * D + c] + tj * sd[k * D + c] - ph.u0[gid * D + c];
+                        in += 0.5 * f * r * r;
+                    }
+                }
                 w += in;
                 s += in;
             }
@@ -280,6 +289,12 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
             if (ph.dyn)
 #pragma unroll
                 for (int c = 0; c < D; ++c) acc[c] += m * (su[k * D + c] - uhat[gid * D + c]);
+            if (ph.fw) {
+                const double f = ph.fw[gid];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (c != 1) acc[c] += f * (su[k * D + c] - ph.u0[gid * D + c]);
+            }
             const bool fx = vd.fixed[gid] != 0;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -320,6 +335,12 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
         if (ph.dyn)
 #pragma unroll
             for (int c = 0; c < D; ++c) acc[c] += m * (u[gid * D + c] - uhat[gid * D + c]);
+        if (ph.fw) {
+            const double f = ph.fw[gid];
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (c != 1) acc[c] += f * (u[gid * D + c] - ph.u0[gid * D + c]);
+        }
         const bool fx = vd.fixed[gid] != 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -519,8 +540,9 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             }
             if (ph.dyn) {
                 const T m = T(vd.mass[gid]);
+                const T mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
 #pragma unroll
-                for (int c = 0; c < D; ++c) acc[c] += m * sv[k * D + c];
+                for (int c = 0; c < D; ++c) acc[c] += (c == 1 ? m : mh) * sv[k * D + c];
             }
             const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
@@ -539,10 +561,15 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
                 vt += ph.s_el * d2 * (double)sv[k * D + 1] * (double)sv[k * D + 1];
             }
             if (ph.dyn) {
-                double v2 = 0.0;
+                double v2 = 0.0, h2 = 0.0;
 #pragma unroll
-                for (int c = 0; c < D; ++c) v2 += (double)sv[k * D + c] * (double)sv[k * D + c];
+                for (int c = 0; c < D; ++c) {
+                    const double q = (double)sv[k * D + c] * (double)sv[k * D + c];
+                    v2 += q;
+                    if (c != 1) h2 += q;
+                }
                 vt += vd.mass[gid] * v2;
+                if (ph.fw) vt += ph.fw[gid] * h2;
             }
             dot += vt;
         }
@@ -582,8 +609,9 @@ __global__ void __launch_bounds__(256) k_fin_hvp(TileDev td, VertDev vd, Phys ph
         }
         if (ph.dyn) {
             const T m = T(vd.mass[gid]);
+            const T mh = ph.fw ? m + T(ph.fw[gid]) : m;
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] += m * vv[c];
+            for (int c = 0; c < D; ++c) acc[c] += (c == 1 ? m : mh) * vv[c];
         }
 #pragma unroll
         for (int c = 0; c < D; ++c) {

@@ -70,13 +70,18 @@ struct VertDev {
 
 // Physical scalars of one evaluation.  s_el scales the potential-energy
 // terms (dt^2 for the backward-Euler incremental potential, else 1); dyn
-// adds the inertia term 1/2 |x - xhat|_M^2 and its derivatives.
+// adds the inertia term 1/2 |x - xhat|_M^2 and its derivatives.  With ground
+// friction (dynamics only), fw is non-null and the potential gains
+// sum_i fw_i/2 |x_i - x0_i|^2 over the horizontal axes (all but y), which is
+// dt^2 k_f |v_h|^2 ReLU(eps - y0_i) at v = (x - x0)/dt.
 struct Phys {
     double mu = 0, lam = 0, k = 0, grav = 0, kc = 0;
     int cpow = 3;
     int log_mode = 0;
     int dyn = 0;
     double s_el = 1.0;
+    const double *fw = nullptr;  // [nv] 2 k_f ReLU(eps - y0), or null: no friction
+    const double *u0 = nullptr;  // [nv][dim] displacement x0 - X of the step's start
 };
 
 // Scalars that the kernels exchange in device memory (no host round trip).
@@ -191,8 +196,12 @@ template <typename Tin, typename Tout>
 void launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
 void launch_mask_copy(const Ctx &c, const double *in, double *out, cudaStream_t s);
 // step backward: xbar0 = M lam - vbar1/dt, vbar0 = dt M lam (masked)
-void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt,
-                             double *xbar0, double *vbar0, cudaStream_t s);
+// u0 = x0 - X and fw = 2 k_f ReLU(eps - y0) for the friction of one step
+void launch_friction_prep(const Ctx &c, const double *x0, double kf, double eps, double *u0, double *fw,
+                          cudaStream_t s);
+void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt, const double *fw,
+                             double kf, const double *x0, const double *x1, double *xbar0, double *vbar0,
+                             cudaStream_t s);
 // b = xbar1 + vbar1/dt
 void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out,
                      cudaStream_t s);

@@ -45,6 +45,7 @@ struct sim_handle {
     double *X = nullptr, *mass = nullptr;
     uint8_t *fixed = nullptr;
     double *u = nullptr, *uhat = nullptr, *g = nullptr, *hp64 = nullptr, *a64 = nullptr;
+    double *fw = nullptr, *u0 = nullptr;  // ground friction of the current step (null when off)
     float *u32 = nullptr, *a32 = nullptr, *hp32 = nullptr;
     void *vd = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr;  // CG vectors in the HVP precision
     double *work = nullptr, *lam = nullptr, *lacc = nullptr, *r64 = nullptr, *Hx = nullptr;
@@ -116,6 +117,10 @@ static Phys make_phys(const sim_handle *h, bool dyn)
     ph.log_mode = h->mat.log_mode;
     ph.dyn = dyn ? 1 : 0;
     ph.s_el = dyn ? h->mat.dt * h->mat.dt : 1.0;
+    if (dyn && h->fw) {
+        ph.fw = h->fw;
+        ph.u0 = h->u0;
+    }
     return ph;
 }
 
@@ -388,6 +393,13 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     CK(h, cudaMemset(h->sc, 0, sizeof(DevScalars)));
     CK(h, cudaMemset(h->u, 0, sizeof(double) * nd));
     CK(h, cudaMemset(h->uhat, 0, sizeof(double) * nd));
+    if (h->mat.dt > 0.0 && h->mat.k_friction > 0.0) {
+        h->fw = (double *)dalloc(h, sizeof(double) * nv);
+        h->u0 = (double *)dalloc(h, sizeof(double) * nd);
+        if (!h->fw || !h->u0) return fail(h, SIM_ENOMEM, "device allocation failed");
+        CK(h, cudaMemset(h->fw, 0, sizeof(double) * nv));
+        CK(h, cudaMemset(h->u0, 0, sizeof(double) * nd));
+    }
     CK(h, cudaMemset(h->vp, 0, vbytes * nd));
     if (h->u32) CK(h, cudaMemset(h->u32, 0, sizeof(float) * nd));
     CK(h, cudaMallocHost((void **)&h->sc_host, sizeof(DevScalars)));
@@ -418,6 +430,8 @@ extern "C" int sim_create(const sim_mesh *mesh, const sim_material *mat, const s
     if (!(mat->dt >= 0.0) || !std::isfinite(mat->mu) || !std::isfinite(mat->lambda) || !std::isfinite(mat->k_muscle) ||
         !std::isfinite(mat->density) || !std::isfinite(mat->gravity) || !std::isfinite(mat->k_contact))
         return fail(nullptr, SIM_EINVAL, "bad material scalar");
+    if (!(mat->k_friction >= 0.0) || !std::isfinite(mat->k_friction) || !std::isfinite(mat->eps_friction))
+        return fail(nullptr, SIM_EINVAL, "k_friction must be finite and >= 0, eps_friction finite");
     if (opt && opt->precision != SIM_PREC_FP64 && opt->precision != SIM_PREC_MIXED)
         return fail(nullptr, SIM_EINVAL, "precision must be SIM_PREC_FP64 or SIM_PREC_MIXED");
     sim_handle *h = new sim_handle();
@@ -775,6 +789,7 @@ extern "C" int sim_newton_solve(sim_handle *h, const double *x_init, const doubl
     int rc;
     if ((rc = set_activation(h, a, s))) return rc;
     if (dyn) launch_uhat(h->ctx, x0, v0, h->mat.dt, h->uhat, s);
+    if (dyn && h->fw) launch_friction_prep(h->ctx, x0, h->mat.k_friction, h->mat.eps_friction, h->u0, h->fw, s);
     if ((rc = set_state(h, x_init, true, s))) return rc;
     const int status = is_mixed(h) ? newton_impl<float>(h, dyn, st, s) : newton_impl<double>(h, dyn, st, s);
     if (status == SIM_ECUDA) return status;
@@ -835,11 +850,12 @@ extern "C" int sim_step_backward(sim_handle *h, const double *x0, const double *
                                  sim_solve_stats *st, void *stream)
 {
     CHECK_H(h);
-    (void)x0;
-    (void)v0;  // the backward only needs the converged state x1
+    (void)v0;  // the backward needs the converged state x1, and x0 only for friction
     if (!(h->mat.dt > 0.0)) return fail(h, SIM_EINVAL, "sim_step_backward needs dt > 0");
     if (!x1 || !a || !xbar1 || !vbar1 || !xbar0 || !vbar0 || !abar) return fail(h, SIM_EINVAL, "null argument");
+    if (h->fw && !x0) return fail(h, SIM_EINVAL, "friction needs x0 in the step backward");
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->fw) launch_friction_prep(h->ctx, x0, h->mat.k_friction, h->mat.eps_friction, h->u0, h->fw, s);
     const double dt = h->mat.dt;
     const int64_t nd = h->nv * h->dim;
     // b = xbar1 + vbar1/dt lives in h->lam until the adjoint overwrites it
@@ -848,7 +864,7 @@ extern "C" int sim_step_backward(sim_handle *h, const double *x0, const double *
     CKL(h);
     int rc = sim_adjoint_solve(h, x1, a, h->lam, h->lam, st, stream);
     if (rc != SIM_OK) return rc;
-    launch_step_bwd_combine(h->ctx, h->lam, vbar1, dt, xbar0, vbar0, s);
+    launch_step_bwd_combine(h->ctx, h->lam, vbar1, dt, h->fw, h->mat.k_friction, x0, x1, xbar0, vbar0, s);
     CKL(h);
     return sim_param_vjp(h, x1, h->lam, abar, stream);
 }

@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
             }
             if (ph.dyn) {
                 const T m = T(vd.mass[i]);
+                const T mh = ph.fw ? m + T(ph.fw[i]) : m;
 #pragma unroll
-                for (int c = 0; c < D; ++c) a[c] += m * p[i * D + c];
+                for (int c = 0; c < D; ++c) a[c] += (c == 1 ? m : mh) * p[i * D + c];
             }
             if (fx)
 #pragma unroll
@@ -290,18 +291,44 @@ __global__ void k_mask_copy(int64_t nv, int dim, const uint8_t *__restrict__ fix
         out[i] = fixed[i / dim] ? 0.0 : in[i];
 }
 
+// Friction data of one backward-Euler step: the start displacement
+// u0 = x0 - X and the weight fw = 2 k_f ReLU(eps - y0) of every vertex.
+__global__ void k_friction_prep(int64_t nv, int dim, const double *__restrict__ x0, const double *__restrict__ X,
+                                double kf, double eps, double *__restrict__ u0, double *__restrict__ fw)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < dim; ++c) u0[i * dim + c] = x0[i * dim + c] - X[i * dim + c];
+        const double r = eps - x0[i * dim + 1];
+        fw[i] = r > 0.0 ? 2.0 * kf * r : 0.0;
+    }
+}
+
+// xbar0 = M lambda - vbar1/dt, vbar0 = dt M lambda, plus, with friction
+// (fw non-null), the derivative of fw_i (x1 - x0)_h by x0: fw_i lambda_h on
+// the horizontal axes and 2 k_f [y0 < eps] lambda_h . (x1 - x0)_h on y.
 __global__ void k_step_bwd_combine(int64_t nv, int dim, const uint8_t *__restrict__ fixed,
                                    const double *__restrict__ mass, const double *__restrict__ lam,
-                                   const double *__restrict__ vbar1, double dt, double *__restrict__ xbar0,
-                                   double *__restrict__ vbar0)
+                                   const double *__restrict__ vbar1, double dt, const double *__restrict__ fw,
+                                   double kf, const double *__restrict__ x0, const double *__restrict__ x1,
+                                   double *__restrict__ xbar0, double *__restrict__ vbar0)
 {
-    const int64_t n = nv * dim;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = i / dim;
-        const double ml = mass[v] * lam[i];
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
         const bool fx = fixed[v] != 0;
-        xbar0[i] = fx ? 0.0 : ml - vbar1[i] / dt;
-        vbar0[i] = fx ? 0.0 : dt * ml;
+        const double m = mass[v];
+        const double f = fw ? fw[v] : 0.0;
+        double ysum = 0.0;
+        for (int c = 0; c < dim; ++c) {
+            const int64_t i = v * dim + c;
+            const double l = lam[i];
+            double xb = m * l - vbar1[i] / dt;
+            if (c != 1 && f > 0.0) {
+                xb += f * l;
+                ysum += l * (x1[i] - x0[i]);
+            }
+            xbar0[i] = fx ? 0.0 : xb;
+            vbar0[i] = fx ? 0.0 : dt * m * l;
+        }
+        if (f > 0.0 && !fx) xbar0[v * dim + 1] += 2.0 * kf * ysum;
     }
 }
 
@@ -463,12 +490,20 @@ void launch_mask_copy(const Ctx &c, const double *in, double *out, cudaStream_t 
     k_mask_copy<<<vec_grid(c.nv * c.dim), 256, 0, s>>>(c.nv, c.dim, c.vd.fixed, in, out);
 }
 
-void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt, double *xbar0,
-                             double *vbar0, cudaStream_t s)
+void launch_friction_prep(const Ctx &c, const double *x0, double kf, double eps, double *u0, double *fw,
+                          cudaStream_t s)
 {
     c.n_launch += 1;
-    k_step_bwd_combine<<<vec_grid(c.nv * c.dim), 256, 0, s>>>(c.nv, c.dim, c.vd.fixed, c.vd.mass, lam, vbar1, dt,
-                                                              xbar0, vbar0);
+    k_friction_prep<<<vec_grid(c.nv), 256, 0, s>>>(c.nv, c.dim, x0, c.vd.X, kf, eps, u0, fw);
+}
+
+void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar1, double dt, const double *fw,
+                             double kf, const double *x0, const double *x1, double *xbar0, double *vbar0,
+                             cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_step_bwd_combine<<<vec_grid(c.nv), 256, 0, s>>>(c.nv, c.dim, c.vd.fixed, c.vd.mass, lam, vbar1, dt, fw, kf, x0,
+                                                     x1, xbar0, vbar0);
 }
 
 void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out, cudaStream_t s)
