@@ -18,12 +18,13 @@ pytestmark = pytest.mark.gpu
 K_F, EPS_F = 2e3, 0.01
 
 
-def _fric(kind="tri", seed=51):
+def _fric(kind="tri", seed=51, cpow=3):
     if kind == "tri":
         p = synth.make_small2d(8, 4, fix_bottom=False, seed=seed)
     else:
         p = synth.make_small3d(3, 2, 3, split=6, fix_bottom=False, seed=seed)
-    p.k_contact, p.contact_power, p.dt = 1e6, 3, 1.0 / 30.0
+    # cpow 2 is the paper's one-sided quadratic collision k_c ReLU(-y)^2
+    p.k_contact, p.contact_power, p.dt = (1e6 if cpow == 3 else 1e5), cpow, 1.0 / 30.0
     p.k_friction, p.eps_friction = K_F, EPS_F
     return p
 
@@ -39,10 +40,11 @@ def _start(p, rng):
     return x0, v0
 
 
+@pytest.mark.parametrize("cpow", [2, 3])
 @pytest.mark.parametrize("kind", ["tri", "tet"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_friction_step_and_backward(kind, precision):
-    p = _fric(kind)
+def test_friction_step_and_backward(kind, precision, cpow):
+    p = _fric(kind, cpow=cpow)
     sim = _sim(p, precision, tile_elems=16, adjoint_rtol=1e-10 if precision == "fp64" else 1e-7)
     m = oracle.make_model(p)
     rng = np.random.default_rng(52)
@@ -102,12 +104,13 @@ def test_friction_rollout_bptt(precision):
         assert np.linalg.norm(host(got) - ref) <= tol * np.linalg.norm(ref)
 
 
-def test_friction_batch_matches_oracle():
+@pytest.mark.parametrize("cpow", [2, 3])
+def test_friction_batch_matches_oracle(cpow):
     from paper_2102_05791_gb300.api import Batch
     probs = []
     for i, (nx, ny, mu) in enumerate([(4, 2, 1e4), (7, 3, 7e3), (5, 2, 1.6e4)]):
         p = synth.make_small2d(nx, ny, fix_bottom=False, seed=56 + i)
-        p.k_contact, p.contact_power, p.dt = 1e6, 3, 1.0 / 30.0
+        p.k_contact, p.contact_power, p.dt = (1e6 if cpow == 3 else 1e5), cpow, 1.0 / 30.0
         p.k_friction, p.eps_friction = K_F, EPS_F
         p.mu, p.lam = mu, 4.0 * mu
         probs.append(p)
