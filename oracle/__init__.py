@@ -49,6 +49,7 @@ class _Model(C.Structure):
         ("gravity", C.c_double), ("k_contact", C.c_double),
         ("contact_power", C.c_int), ("log_mode", C.c_int),
         ("h", C.c_double), ("xhat", C.c_void_p),
+        ("muscle_model", C.c_int),
         ("k_friction", C.c_double), ("eps_friction", C.c_double), ("x0", C.c_void_p),
     ]
 
@@ -75,7 +76,7 @@ def lib():
         L.or_energy.restype = C.c_double
         L.or_grad.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
         L.or_hvp.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
-        L.or_param_vjp.argtypes = [C.POINTER(_Model), dp, dp, dp]
+        L.or_param_vjp.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
         L.or_cg.argtypes = [C.POINTER(_Model), dp, dp, dp, dp, C.c_double, C.c_int, dp]
         L.or_cg.restype = C.c_int
         L.or_newton.argtypes = [C.POINTER(_Model), dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
@@ -117,6 +118,7 @@ class Model:
     k_friction: float = 0.0
     eps_friction: float = 0.01
     x0: np.ndarray | None = None
+    muscle_model: int = 0
 
     @property
     def nv(self):
@@ -140,6 +142,7 @@ class Model:
         m.contact_power, m.log_mode = int(self.contact_power), int(self.log_mode)
         m.h = self.h
         m.xhat = _p(self.xhat)
+        m.muscle_model = int(self.muscle_model)
         m.k_friction, m.eps_friction = self.k_friction, self.eps_friction
         m.x0 = _p(self.x0)
         return m
@@ -171,10 +174,12 @@ class Model:
         lib().or_hvp(C.byref(self._c()), _p(x), _p(a), _p(v), _p(out))
         return out
 
-    def param_vjp(self, x, lam):
+    def param_vjp(self, x, lam, a=None):
+        """dL/da at x for adjoint lam (a is needed by the spring muscle only)."""
         x, lam = _f64(x), _f64(lam)
+        a = np.zeros(self.ne) if a is None else _f64(a)
         out = np.zeros(self.ne)
-        lib().or_param_vjp(C.byref(self._c()), _p(x), _p(lam), _p(out))
+        lib().or_param_vjp(C.byref(self._c()), _p(x), _p(a), _p(lam), _p(out))
         return out
 
     # -- solvers ---------------------------------------------------------------
@@ -241,7 +246,8 @@ def make_model(prob, log_mode=None, with_fixed=True, h=None, xhat=None) -> Model
                  log_mode=int(prob.log_mode if log_mode is None else log_mode),
                  h=float(prob.dt if h is None else h), xhat=None if xhat is None else _f64(xhat),
                  k_friction=float(getattr(prob, "k_friction", 0.0)),
-                 eps_friction=float(getattr(prob, "eps_friction", 0.01)))
+                 eps_friction=float(getattr(prob, "eps_friction", 0.01)),
+                 muscle_model=int(getattr(prob, "muscle_model", 0)))
 
 
 # ---------------------------------------------------------------------------
@@ -263,7 +269,7 @@ def quasistatic_forward_backward(model: Model, a, target, rtol=1e-8, adj_rtol=1e
     x, st = model.newton(a, rtol=rtol)
     g = mean_loss_grad(x, target)
     lam, it = model.adjoint(x, a, g, rtol=adj_rtol)
-    return x, lam, model.param_vjp(x, lam), st
+    return x, lam, model.param_vjp(x, lam, a), st
 
 
 # ---------------------------------------------------------------------------
@@ -311,7 +317,7 @@ def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12):
         fx = model.fixed.astype(bool)
         xbar0[fx] = 0.0
         vbar0[fx] = 0.0
-    abar = m.param_vjp(x1, lam)
+    abar = m.param_vjp(x1, lam, a)
     return xbar0, vbar0, abar
 
 

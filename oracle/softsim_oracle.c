@@ -23,8 +23,10 @@
  *
  * Readings where the paper is silent: the quadratic stand-in for log J is
  * the second-order Taylor polynomial q(J) = (J-1) - (J-1)^2/2 (Sec. 2 names
- * a quadratic approximation without giving it); the muscle is the
- * per-element contractile term rather than the paper's 1D spring.
+ * a quadratic approximation without giving it).  Two muscle models, both
+ * integrated over the element like Psi: the contractile term (k/2) a |F f|^2,
+ * and the paper's active spring (Eq. active-spring-potential) with the
+ * fiber's stretch |F f| = l / l0 (f a unit rest fiber), (k/2)(|F f|/a - 1)^2.
  *
  * Everything is a direct element loop with "+=" into vertex arrays.
  */
@@ -46,6 +48,7 @@ typedef struct {
     int log_mode;               /* 0 exact log J, 1 quadratic q(J) */
     double h;                   /* time step; 0 = quasistatic */
     const double *xhat;         /* [nv][d] inertial target x0 + h v0 (dynamics only) */
+    int muscle_model;           /* 0: contractile (k/2) a |F f|^2; 1: active spring (k/2)(|F f|/a - 1)^2 */
     double k_friction;          /* ground friction stiffness (dynamics only; 0 = off) */
     double eps_friction;        /* contact tolerance of the friction weight */
     const double *x0;           /* [nv][d] previous positions (dynamics only) */
@@ -208,6 +211,72 @@ void or_mass(int d, long nv, long ne, const int *T, const double *W, double rho,
         for (int k = 0; k <= d; ++k) m[T[e * (d + 1) + k]] += rho * W[e] / (d + 1);
 }
 
+/* ---------------------------------------------------------------- muscle */
+
+/* Muscle energy density of one element as a function of q = F f. */
+static double muscle_psi(const or_model *M, double a, const double *q)
+{
+    int d = M->d;
+    double q2 = 0.0;
+    for (int i = 0; i < d; ++i) q2 += q[i] * q[i];
+    if (M->muscle_model == 0) return 0.5 * M->k_muscle * a * q2;
+    double r = sqrt(q2) / a - 1.0;
+    return 0.5 * M->k_muscle * r * r;
+}
+
+/* d psi / d q. */
+static void muscle_dpsi(const or_model *M, double a, const double *q, double *out)
+{
+    int d = M->d;
+    if (M->muscle_model == 0) {
+        for (int i = 0; i < d; ++i) out[i] = M->k_muscle * a * q[i];
+        return;
+    }
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s += q[i] * q[i];
+    s = sqrt(s);
+    double r = s / a - 1.0;
+    /* k r dr/dq, dr/dq = q / (a s) */
+    for (int i = 0; i < d; ++i) out[i] = M->k_muscle * r * q[i] / (a * s);
+}
+
+/* (d^2 psi / dq^2) dq: the spring's Hessian is k/(a^2 s^2) q q^T (the
+ * squared slope of r) plus k r times the Hessian of s/a,
+ * (I/s - q q^T/s^3)/a. */
+static void muscle_d2psi(const or_model *M, double a, const double *q, const double *dq, double *out)
+{
+    int d = M->d;
+    if (M->muscle_model == 0) {
+        for (int i = 0; i < d; ++i) out[i] = M->k_muscle * a * dq[i];
+        return;
+    }
+    double s2 = 0.0, qdq = 0.0;
+    for (int i = 0; i < d; ++i) {
+        s2 += q[i] * q[i];
+        qdq += q[i] * dq[i];
+    }
+    double s = sqrt(s2);
+    double r = s / a - 1.0;
+    double k = M->k_muscle;
+    for (int i = 0; i < d; ++i)
+        out[i] = k / (a * a * s2) * qdq * q[i] + k * r / a * (dq[i] / s - qdq * q[i] / (s2 * s));
+}
+
+/* d^2 psi / dq da. */
+static void muscle_dpsi_da(const or_model *M, double a, const double *q, double *out)
+{
+    int d = M->d;
+    if (M->muscle_model == 0) {
+        for (int i = 0; i < d; ++i) out[i] = M->k_muscle * q[i];
+        return;
+    }
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s += q[i] * q[i];
+    s = sqrt(s);
+    /* d/da of k (s/a - 1) q / (a s) = k q / s * d/da (s/a^2 - 1/a) */
+    for (int i = 0; i < d; ++i) out[i] = M->k_muscle * q[i] / s * (-2.0 * s / (a * a * a) + 1.0 / (a * a));
+}
+
 /* ---------------------------------------------------------------- energy */
 
 /* Ground friction (Sec. 4.2, Eq. energy-friction): with the velocity
@@ -271,13 +340,10 @@ double or_energy(const or_model *M, const double *x, const double *a, double *ab
         }
         double psi = 0.5 * M->mu * (I1 - d) - M->mu * l + 0.5 * M->lam * l * l;
         const double *f = M->fiber + e * d;
-        double Ff2 = 0.0;
-        for (int i = 0; i < d; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < d; ++j) s += F[i][j] * f[j];
-            Ff2 += s * s;
-        }
-        double psim = 0.5 * M->k_muscle * a[e] * Ff2;
+        double q[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) q[i] += F[i][j] * f[j];
+        double psim = muscle_psi(M, a[e], q);
         double w = M->W[e] * (psi + psim);
         E += w;
         S += fabs(w);
@@ -357,11 +423,12 @@ void or_grad(const or_model *M, const double *x, const double *a, double *g, dou
         mul_d(d, Ds, B, F);
         pk1(M, F, P);
         const double *f = M->fiber + e * d;
-        double Ff[3] = {0, 0, 0};
+        double Ff[3] = {0, 0, 0}, dpsi[3];
         for (int i = 0; i < d; ++i)
             for (int j = 0; j < d; ++j) Ff[i] += F[i][j] * f[j];
+        muscle_dpsi(M, a[e], Ff, dpsi);
         for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) P[i][j] += M->k_muscle * a[e] * Ff[i] * f[j];
+            for (int j = 0; j < d; ++j) P[i][j] += dpsi[i] * f[j];
         transpose_d(d, B, BT);
         mul_d(d, P, BT, G);
         for (int i = 0; i < d; ++i)
@@ -473,11 +540,15 @@ void or_hvp(const or_model *M, const double *x, const double *a, const double *v
         mul_d(d, dDs, B, dF);
         dpk1(M, F, dF, dP);
         const double *f = M->fiber + e * d;
-        double dFf[3] = {0, 0, 0};
+        double Ff[3] = {0, 0, 0}, dFf[3] = {0, 0, 0}, d2[3];
         for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) dFf[i] += dF[i][j] * f[j];
+            for (int j = 0; j < d; ++j) {
+                Ff[i] += F[i][j] * f[j];
+                dFf[i] += dF[i][j] * f[j];
+            }
+        muscle_d2psi(M, a[e], Ff, dFf, d2);
         for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) dP[i][j] += M->k_muscle * a[e] * dFf[i] * f[j];
+            for (int j = 0; j < d; ++j) dP[i][j] += d2[i] * f[j];
         transpose_d(d, B, BT);
         mul_d(d, dP, BT, G);
         for (int i = 0; i < d; ++i)
@@ -505,10 +576,11 @@ void or_hvp(const or_model *M, const double *x, const double *a, const double *v
 
 /* ---------------------------------------------------------------- param VJP */
 
-/* dL/da_e = -lambda^T d(grad g)/da_e = -s W_e k (F f) . (dF(lambda) f), where
+/* dL/da_e = -lambda^T d(grad E)/da_e = -s W_e (d^2 psi/dq da) . (dF(lambda) f)
+ * with q = F f (for the contractile term k (F f) . (dF(lambda) f)), where
  * s = h^2 for the incremental potential and 1 otherwise (Eq. dLda-re-ordered
  * with the muscle term as the only a-dependent energy). */
-void or_param_vjp(const or_model *M, const double *x, const double *lam, double *dLda)
+void or_param_vjp(const or_model *M, const double *x, const double *a, const double *lam, double *dLda)
 {
     int d = M->d;
     double s = M->h > 0.0 ? M->h * M->h : 1.0;
@@ -520,16 +592,16 @@ void or_param_vjp(const or_model *M, const double *x, const double *lam, double 
         mul_d(d, Ds, B, F);
         mul_d(d, dDs, B, dF);
         const double *f = M->fiber + e * d;
-        double dot = 0.0;
-        for (int i = 0; i < d; ++i) {
-            double Ff = 0.0, dFf = 0.0;
+        double Ff[3] = {0, 0, 0}, dFf[3] = {0, 0, 0}, mix[3];
+        for (int i = 0; i < d; ++i)
             for (int j = 0; j < d; ++j) {
-                Ff += F[i][j] * f[j];
-                dFf += dF[i][j] * f[j];
+                Ff[i] += F[i][j] * f[j];
+                dFf[i] += dF[i][j] * f[j];
             }
-            dot += Ff * dFf;
-        }
-        dLda[e] = -s * M->W[e] * M->k_muscle * dot;
+        muscle_dpsi_da(M, a[e], Ff, mix);
+        double dot = 0.0;
+        for (int i = 0; i < d; ++i) dot += mix[i] * dFf[i];
+        dLda[e] = -s * M->W[e] * dot;
     }
 }
 

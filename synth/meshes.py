@@ -57,6 +57,7 @@ class SynthProblem:
     contact_power: int = 3
     dt: float = 0.0
     log_mode: int = 0      # 0 = exact log J, 1 = quadratic approximation
+    muscle_model: int = 0     # 0 = contractile (k/2) a |Ff|^2, 1 = active spring (k/2)(|Ff|/a - 1)^2
     k_friction: float = 0.0   # ground friction stiffness (dynamics only)
     eps_friction: float = 0.01  # height below which friction acts
     extra: dict = dataclasses.field(default_factory=dict)
