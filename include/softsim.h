@@ -57,6 +57,7 @@ enum {
 
 enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1 };
 enum { SIM_LOG_EXACT = 0, SIM_LOG_QUAD = 1 };
+enum { SIM_MUSCLE_CONTRACTILE = 0, SIM_MUSCLE_SPRING = 1 };
 
 typedef struct sim_handle sim_handle;
 
@@ -81,7 +82,11 @@ typedef struct {
  * friction of Sec. 4.2, dt^2 sum_i k_f |v_h,i|^2 ReLU(eps_friction - y0_i),
  * with v = (x - x0)/dt and v_h its horizontal part (every axis but y): the
  * damping acts on vertices that started the step within eps_friction of
- * the ground (or below it).  A zero-initialised struct has friction off. */
+ * the ground (or below it).  A zero-initialised struct has friction off.
+ * muscle_model selects psi_m: SIM_MUSCLE_CONTRACTILE (k/2) a |F f|^2, or
+ * SIM_MUSCLE_SPRING (k/2)(|F f|/a - 1)^2, the active spring of Eq.
+ * active-spring-potential with |F f| = l/l0 the fiber stretch; it needs
+ * a > 0 (a <= 0 makes the energy non-finite: SIM_ENAN). */
 typedef struct {
     double mu, lambda;        /* Lame parameters */
     double k_muscle;          /* muscle stiffness k */
@@ -94,6 +99,7 @@ typedef struct {
     const double *fiber;      /* HOST [n_elem][dim] unit fiber directions */
     double k_friction;        /* ground friction stiffness k_f (0 = off) */
     double eps_friction;      /* height below which friction acts */
+    int muscle_model;         /* SIM_MUSCLE_CONTRACTILE (0) or SIM_MUSCLE_SPRING */
 } sim_material;
 
 typedef struct {
@@ -176,10 +182,13 @@ int sim_adjoint_solve(sim_handle *h, const double *x_star, const double *a, cons
                       double *lambda, sim_solve_stats *stats, void *stream);
 
 /* Parameter VJP (Eq. dLda-re-ordered): dLda_e = -s lambda^T d(grad E)/da_e
- * = -s W_e k (F_e f_e) . (dF_e(lambda) f_e), s = dt^2 for backward Euler and
- * 1 otherwise.  Output [n_elem] double in the caller's element order. */
-int sim_param_vjp(sim_handle *h, const double *x_star, const double *lambda, double *dLda,
-                  void *stream);
+ * = -s W_e (d2psi_m/dq da) . (dF_e(lambda) f_e) with q = F_e f_e, i.e.
+ * k q for the contractile muscle and k (1/a^2 - 2|q|/a^3) q/|q| for the
+ * spring; s = dt^2 for backward Euler and 1 otherwise.  a: DEVICE
+ * [n_elem] activations at which x_star was solved.  Output [n_elem] double
+ * in the caller's element order. */
+int sim_param_vjp(sim_handle *h, const double *x_star, const double *a, const double *lambda,
+                  double *dLda, void *stream);
 
 /* One backward-Euler step (Eq. opt-be), dt > 0 only: x1 = argmin of the
  * incremental potential started from x0, v1 = (x1 - x0)/dt.  x1 and v1 must

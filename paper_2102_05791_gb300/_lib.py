@@ -15,6 +15,7 @@ SIM_OK, SIM_EINVAL, SIM_ECUDA, SIM_EINVERTED, SIM_ENOTCONVERGED, SIM_ELINESEARCH
     0, -1, -2, -3, -4, -5, -6, -7)
 SIM_PREC_FP64, SIM_PREC_MIXED = 0, 1
 SIM_LOG_EXACT, SIM_LOG_QUAD = 0, 1
+SIM_MUSCLE_CONTRACTILE, SIM_MUSCLE_SPRING = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EINVERTED", -4: "ENOTCONVERGED",
                 -5: "ELINESEARCH", -6: "ENAN", -7: "ENOMEM"}
@@ -38,7 +39,8 @@ class SimMaterial(C.Structure):
     _fields_ = [("mu", C.c_double), ("lambda_", C.c_double), ("k_muscle", C.c_double),
                 ("density", C.c_double), ("gravity", C.c_double), ("k_contact", C.c_double),
                 ("contact_power", C.c_int), ("log_mode", C.c_int), ("dt", C.c_double),
-                ("fiber", C.c_void_p), ("k_friction", C.c_double), ("eps_friction", C.c_double)]
+                ("fiber", C.c_void_p), ("k_friction", C.c_double), ("eps_friction", C.c_double),
+                ("muscle_model", C.c_int)]
 
 
 class SimOptions(C.Structure):
@@ -81,7 +83,7 @@ def load(path: str | None = None):
     L.sim_hvp.argtypes = [H, vp, vp, vp, vp, vp]
     L.sim_newton_solve.argtypes = [H, vp, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_adjoint_solve.argtypes = [H, vp, vp, vp, vp, C.POINTER(SimStats), vp]
-    L.sim_param_vjp.argtypes = [H, vp, vp, vp, vp]
+    L.sim_param_vjp.argtypes = [H, vp, vp, vp, vp, vp]
     L.sim_step_forward.argtypes = [H, vp, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_step_backward.argtypes = [H, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_rollout.argtypes = [H, i, vp, vp, vp, i, vp, vp, vp, vp, C.POINTER(SimStats), vp]

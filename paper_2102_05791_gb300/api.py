@@ -45,7 +45,7 @@ class Simulator:
     """
 
     def __init__(self, X, T, fixed=None, fiber=None, *, mu, lam, k_muscle=0.0, density=0.0, gravity=0.0,
-                 k_contact=0.0, contact_power=3, log_mode=0, dt=0.0, k_friction=0.0, eps_friction=0.01,
+                 k_contact=0.0, contact_power=3, log_mode=0, dt=0.0, k_friction=0.0, eps_friction=0.01, muscle_model=0,
                  precision="mixed", newton_rtol=1e-8, newton_forcing=0.5,
                  adjoint_rtol=1e-6, max_newton=100, max_cg=500, max_adjoint_cg=0, max_ls=30, tile_elems=0,
                  threads=0, device=None):
@@ -56,7 +56,8 @@ class Simulator:
             with torch.cuda.device(self.device):
                 tile_elems, threads = autotune.best_tile_shape(
                     X, T, fixed, fiber, precision=precision, mu=mu, lam=lam, k_muscle=k_muscle, density=density,
-                    gravity=gravity, k_contact=k_contact, contact_power=contact_power, log_mode=log_mode, dt=dt)
+                    gravity=gravity, k_contact=k_contact, contact_power=contact_power, log_mode=log_mode, dt=dt,
+                    muscle_model=muscle_model)
         self.tile_shape = (int(tile_elems), int(threads))
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
         T = np.ascontiguousarray(np.asarray(T, dtype=np.int32))
@@ -69,7 +70,8 @@ class Simulator:
                          None if fx is None else fx.ctypes.data)
         mat = L.SimMaterial(float(mu), float(lam), float(k_muscle), float(density), float(gravity),
                             float(k_contact), int(contact_power), int(log_mode), float(dt),
-                            None if fb is None else fb.ctypes.data, float(k_friction), float(eps_friction))
+                            None if fb is None else fb.ctypes.data, float(k_friction), float(eps_friction),
+                            int(muscle_model))
         opt = L.SimOptions()
         self._lib.sim_default_options(C.byref(opt))
         opt.precision = L.SIM_PREC_MIXED if precision == "mixed" else L.SIM_PREC_FP64
@@ -138,10 +140,11 @@ class Simulator:
         self._check("sim_hvp", self._lib.sim_hvp(self._h, _ptr(x), _ptr(a), _ptr(v), _ptr(out), _stream()))
         return out
 
-    def param_vjp(self, x_star, lam):
-        x_star, lam = self._vec(x_star), self._vec(lam, name="lambda")
+    def param_vjp(self, x_star, a, lam):
+        x_star, a, lam = self._vec(x_star), self._elem(a), self._vec(lam, name="lambda")
         out = torch.empty(self.n_elem, dtype=torch.float64, device=self.device)
-        self._check("sim_param_vjp", self._lib.sim_param_vjp(self._h, _ptr(x_star), _ptr(lam), _ptr(out), _stream()))
+        self._check("sim_param_vjp", self._lib.sim_param_vjp(self._h, _ptr(x_star), _ptr(a), _ptr(lam), _ptr(out),
+                                                             _stream()))
         return out
 
     # -- solves ------------------------------------------------------------------
@@ -270,7 +273,7 @@ class Batch:
             meshes[i] = L.SimMesh(X.shape[1], X.shape[0], T.shape[0], X.ctypes.data, T.ctypes.data, fx.ctypes.data)
             mats[i] = L.SimMaterial(p.mu, p.lam, p.k_muscle, p.density, p.gravity, p.k_contact, p.contact_power,
                                     p.log_mode, p.dt, fb.ctypes.data, float(getattr(p, "k_friction", 0.0)),
-                                    float(getattr(p, "eps_friction", 0.01)))
+                                    float(getattr(p, "eps_friction", 0.01)), int(getattr(p, "muscle_model", 0)))
         opt = L.SimOptions()
         self._lib.sim_default_options(C.byref(opt))
         opt.newton_rtol, opt.adjoint_rtol = float(newton_rtol), float(adjoint_rtol)
@@ -340,7 +343,7 @@ class QuasistaticSolve(torch.autograd.Function):
     def backward(ctx, gx):
         x, a = ctx.saved_tensors
         lam, _ = ctx.sim.adjoint(x, a.detach().contiguous(), gx.contiguous())
-        return None, ctx.sim.param_vjp(x, lam)
+        return None, ctx.sim.param_vjp(x, a.detach().contiguous(), lam)
 
 
 class BEStep(torch.autograd.Function):

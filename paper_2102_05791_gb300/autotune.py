@@ -30,11 +30,12 @@ def cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "softsim", "autotune.json"))
 
 
-def _key(dim: int, n_elem: int, precision: str) -> str:
+def _key(dim: int, n_elem: int, precision: str, muscle_model: int = 0) -> str:
     import torch
     name = torch.cuda.get_device_name(torch.cuda.current_device())
     bucket = int(math.log2(max(n_elem, 1)))
-    return f"{name}|d{dim}|e2^{bucket}|{precision}"
+    # the spring muscle stages the fiber too (more shared memory per tile)
+    return f"{name}|d{dim}|e2^{bucket}|{precision}" + ("|spring" if muscle_model else "")
 
 
 def _load() -> dict:
@@ -85,7 +86,7 @@ def best_tile_shape(X, T, fixed=None, fiber=None, precision: str = "mixed", cand
     X = np.asarray(X)
     T = np.asarray(T)
     dim = X.shape[1]
-    key = _key(dim, len(T), precision)
+    key = _key(dim, len(T), precision, int(material.get("muscle_model", 0)))
     cache = _load() if use_cache else {}
     if key in cache:
         return tuple(cache[key]["best"])

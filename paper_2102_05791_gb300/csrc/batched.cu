@@ -49,7 +49,7 @@ struct BatchDev {
     const double *mu = nullptr, *lam = nullptr;      // [M]
     double k = 0, grav = 0, kc = 0, dt = 0;
     double kf = 0, feps = 0;  // ground friction k_f and its height; kf == 0: off
-    int cpow = 3, log_mode = 0;
+    int cpow = 3, log_mode = 0, muscle = 0;
     double newton_rtol = 1e-8, adj_rtol = 1e-6;
     int max_newton = 100, max_cg = 500, max_adj_cg = 2000, max_ls = 30;
     // workspace [V][d]
@@ -162,6 +162,15 @@ __device__ __forceinline__ double contact_d2(double y, double kc, int p)
 
 // ---------------------------------------------------------------- passes (CTA-wide)
 
+// Muscle energy density from |F f|^2: contractile (k/2) a |F f|^2 or the
+// active spring (k/2)(|F f|/a - 1)^2.
+__device__ __forceinline__ double muscle_psi(const BatchDev &b, double a, double Ff2)
+{
+    if (!b.muscle) return 0.5 * b.k * a * Ff2;
+    const double r = sqrt(Ff2) / a - 1.0;
+    return 0.5 * b.k * r * r;
+}
+
 // FP64 gradient of the incremental potential at u; returns |g|^2 over free entries.
 template <int D>
 __device__ double grad_pass(const BatchDev &b, const Mesh &m, const double *a_t, double *red)
@@ -187,7 +196,13 @@ __device__ double grad_pass(const BatchDev &b, const Mesh &m, const double *a_t,
             for (int q = 0; q < D; ++q) s += F[i][q] * f[q];
             Ff[i] = s;
         }
-        const double ka = b.k * a_t[e];
+        double ka = b.k * a_t[e];  // dpsi_m/dq = ka q
+        if (b.muscle) {
+            double s2 = 0.0, c2;
+#pragma unroll
+            for (int i = 0; i < D; ++i) s2 += Ff[i] * Ff[i];
+            spring_terms<double>(W != 0.0, b.k, a_t[e], sqrt(s2), ka, c2);
+        }
         double G[D][D];
 #pragma unroll
         for (int i = 0; i < D; ++i)
@@ -270,7 +285,7 @@ __device__ double energy_pass(const BatchDev &b, const Mesh &m, const double *a_
         else
             l = (J - 1.0) - 0.5 * (J - 1.0) * (J - 1.0);
         double w = s_el * W *
-                   (0.5 * m.mu * (I1 - D) - m.mu * l + 0.5 * m.lam * l * l + 0.5 * b.k * a_t[e] * Ff2);
+                   (0.5 * m.mu * (I1 - D) - m.mu * l + 0.5 * m.lam * l * l + muscle_psi(b, a_t[e], Ff2));
         if (b.log_mode == 0 && !(J > 0.0)) w = INFINITY;
         E += w;
         A += fabs(w);
@@ -339,13 +354,32 @@ __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, 
         T l, cc, cp;
         log_terms<T>(b.log_mode, mu, lam, J, l, cc, cp);
         const T ka = T(b.k * a_t[e]);
-        T dvg[D];
+        T dvg[D];  // (d2psi_m/dq2) dq with dq = Dv g
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
-            dvg[i] = ka * s;
+            dvg[i] = s;
+        }
+        if (b.muscle) {  // spring, q = F f = f + Du g
+            T q[D], s2 = T(0), qdq = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                T s = f[i];
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
+                q[i] = s;
+                s2 += s * s;
+                qdq += s * dvg[i];
+            }
+            T c1, c2;
+            spring_terms<T>(W != T(0), T(b.k), T(a_t[e]), sqrt(s2), c1, c2);
+#pragma unroll
+            for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) dvg[i] *= ka;
         }
         T G[D][D];
 #pragma unroll
@@ -605,7 +639,7 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
         edge_of<double, double, D>(b.u, m, lid, Du);
         edge_of<double, double, D>(b.lacc, m, lid, Dl);
         mul<double, D>(Du, B, F, true);
-        double dot = 0.0;
+        double dot = 0.0, s2 = 0.0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             double Ff = 0.0, dFf = 0.0;
@@ -615,8 +649,14 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
                 dFf += Dl[i][q] * gv[q];
             }
             dot += Ff * dFf;
+            s2 += Ff * Ff;
         }
-        abar_t[e] = -h * h * W * b.k * dot;
+        double kq = b.k;  // d2psi_m/dq da = kq q
+        if (b.muscle) {
+            const double s = sqrt(s2), ia = 1.0 / a_t[e];
+            kq = b.k * (ia * ia - 2.0 * s * ia * ia * ia) / s;
+        }
+        abar_t[e] = -h * h * W * kq * dot;
     }
     __syncthreads();
     return status;
@@ -770,11 +810,13 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
         if (mats[m].k_muscle != m0.k_muscle || mats[m].gravity != m0.gravity || mats[m].k_contact != m0.k_contact ||
             mats[m].contact_power != m0.contact_power || mats[m].log_mode != m0.log_mode || mats[m].dt != m0.dt ||
             mats[m].density != m0.density || mats[m].k_friction != m0.k_friction ||
-            mats[m].eps_friction != m0.eps_friction)
+            mats[m].eps_friction != m0.eps_friction || mats[m].muscle_model != m0.muscle_model)
             return bfail(bt, SIM_EINVAL, "batched meshes may differ only in mu and lambda");
     if (!(m0.k_friction >= 0.0) || !std::isfinite(m0.k_friction) || !std::isfinite(m0.eps_friction))
         return bfail(bt, SIM_EINVAL, "k_friction must be finite and >= 0, eps_friction finite");
     if (m0.contact_power != 2 && m0.contact_power != 3) return bfail(bt, SIM_EINVAL, "contact_power must be 2 or 3");
+    if (m0.muscle_model != SIM_MUSCLE_CONTRACTILE && m0.muscle_model != SIM_MUSCLE_SPRING)
+        return bfail(bt, SIM_EINVAL, "muscle_model must be SIM_MUSCLE_CONTRACTILE or SIM_MUSCLE_SPRING");
     const int64_t V = bt->voff[M], E = bt->eoff[M];
     bt->V = V;
     bt->E = E;
@@ -877,6 +919,7 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.feps = m0.eps_friction;
     b.cpow = m0.contact_power;
     b.log_mode = m0.log_mode;
+    b.muscle = m0.muscle_model;
     b.newton_rtol = o.newton_rtol;
     b.adj_rtol = o.adjoint_rtol;
     b.max_newton = o.max_newton;

@@ -142,7 +142,12 @@ __global__ void __launch_bounds__(256) k_tile_energy(TileDev td, ElemDev<double>
                 const double jm = J - 1.0;
                 l = jm - 0.5 * jm * jm;
             }
-            double w = ph.s_el * W * (0.5 * mu * (I1 - D) - mu * l + 0.5 * lam * l * l + 0.5 * ka * Ff2);
+            double musc = 0.5 * ka * Ff2;
+            if (ph.muscle) {
+                const double r = sqrt(Ff2) / a[e] - 1.0;
+                musc = W != 0.0 ? 0.5 * ph.k * r * r : 0.0;
+            }
+            double w = ph.s_el * W * (0.5 * mu * (I1 - D) - mu * l + 0.5 * lam * l * l + musc);
             if (ph.log_mode == 0 && !(J > 0.0)) w = INFINITY;
             Eacc[j] += w;
             Sacc[j] += fabs(w);
@@ -258,7 +263,13 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
             for (int q = 0; q < D; ++q) s += F[i][q] * f[q];
             Ff[i] = s;
         }
-        const double ka = ph.k * a[e];
+        double ka = ph.k * a[e];  // dpsi_m/dq = ka q
+        if (ph.muscle) {
+            double s2 = 0.0, c2;
+#pragma unroll
+            for (int i = 0; i < D; ++i) s2 += Ff[i] * Ff[i];
+            spring_terms<double>(W != 0.0, ph.k, a[e], sqrt(s2), ka, c2);
+        }
         double G[D][D];
 #pragma unroll
         for (int i = 0; i < D; ++i)
@@ -365,11 +376,12 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
 template <typename T, int D>
 struct HvpSmem {
     static constexpr int NF = D * D + D + 1;  // Dm^-1, g, W
+    static constexpr int NF_SPRING = NF + D;  // + the fiber f (the spring needs q = F f)
     size_t e, conn, a, inc, gid, code, linc, u, v, total;
-    __host__ __device__ HvpSmem(int max_te, int max_tv)
+    __host__ __device__ HvpSmem(int max_te, int max_tv, int nf)
     {
         e = 16;  // two mbarriers
-        conn = e + (size_t)NF * max_te * sizeof(T);
+        conn = e + (size_t)nf * max_te * sizeof(T);
         a = conn + (size_t)max_te * 4;
         inc = a + (size_t)max_te * sizeof(T);
         gid = inc + (size_t)max_te * (D + 1) * 2;
@@ -397,7 +409,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     extern __shared__ __align__(128) unsigned char smem[];
     // MTE != 0: the tile capacity is a compile-time constant, so every
     // element-field and corner offset below folds into an immediate
-    const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv);
+    const int NF = ph.muscle ? HvpSmem<T, D>::NF_SPRING : HvpSmem<T, D>::NF;
+    const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv, NF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
     T *sE = reinterpret_cast<T *>(smem + L.e);
     const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
@@ -412,7 +425,6 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
     const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
     const int mte = MTE ? MTE : td.max_te;
-    constexpr int NF = HvpSmem<T, D>::NF;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
@@ -496,13 +508,32 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         T l, cc, cp;
         log_terms<T>(ph.log_mode, mu, lam, J, l, cc, cp);
         const T cpdJ = cp * dJ;
-        T dvg[D];
+        T dvg[D];  // (d2psi_m/dq2) dq with dq = dF f = Dv g
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
-            dvg[i] = ka * s;
+            dvg[i] = s;
+        }
+        if (ph.muscle) {  // spring, with q = F f = f + Du g
+            T q[D], s2 = T(0), qdq = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                T s = sE[(FI<D>::F + i) * mte + le];
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
+                q[i] = s;
+                s2 += s * s;
+                qdq += s * dvg[i];
+            }
+            T c1, c2;
+            spring_terms<T>(W != T(0), kk, sA[le], sqrt(s2), c1, c2);
+#pragma unroll
+            for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) dvg[i] *= ka;
         }
         T G[D][D];
 #pragma unroll
@@ -643,8 +674,8 @@ __global__ void __launch_bounds__(256) k_fin_hvp(TileDev td, VertDev vd, Phys ph
 
 template <int D>
 __global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed, VertDev vd, Phys ph,
-                                                  const double *__restrict__ u, const double *__restrict__ lam,
-                                                  double *__restrict__ out)
+                                                  const double *__restrict__ u, const double *__restrict__ a,
+                                                  const double *__restrict__ lam, double *__restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *su = reinterpret_cast<double *>(smem);
@@ -677,7 +708,7 @@ __global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed
             f[i] = __ldg(ed.field(FI<D>::F + i) + e);
             gv[i] = __ldg(ed.field(FI<D>::G + i) + e);
         }
-        double dot = 0.0;
+        double dot = 0.0, s2 = 0.0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             double Ff = 0.0, dFf = 0.0;
@@ -687,10 +718,17 @@ __global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed
                 dFf += Dl[i][q] * gv[q];  // dF(lam) f = Dlam Dm^-1 f = Dlam g
             }
             dot += Ff * dFf;
+            s2 += Ff * Ff;
         }
         const double W = __ldg(ed.field(FI<D>::W) + e);
         const int32_t pe = td.perm[e];
-        if (pe >= 0) out[pe] = -ph.s_el * W * ph.k * dot;
+        // d2psi/dq da = k q (contractile) or k (1/a^2 - 2 s/a^3)/s q (spring, s = |q|)
+        double kq = ph.k;
+        if (ph.muscle && pe >= 0) {
+            const double s = sqrt(s2), ia = 1.0 / a[e];
+            kq = ph.k * (ia * ia - 2.0 * s * ia * ia * ia) / s;
+        }
+        if (pe >= 0) out[pe] = -ph.s_el * W * kq * dot;
     }
 }
 
@@ -740,7 +778,10 @@ const ElemDev<double> &edev<double>(const Ctx &c) { return c.e64; }
 template <typename T>
 size_t hvp_smem(const Ctx &c)
 {
-    return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv).total : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv).total;
+    const int nf2 = c.muscle ? HvpSmem<T, 2>::NF_SPRING : HvpSmem<T, 2>::NF;
+    const int nf3 = c.muscle ? HvpSmem<T, 3>::NF_SPRING : HvpSmem<T, 3>::NF;
+    return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv, nf2).total
+                      : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv, nf3).total;
 }
 
 // Resident CTAs per SM that the tile's shared memory allows (at most 4);
@@ -830,15 +871,15 @@ void launch_hvp_finalize_only(const Ctx &c, const Phys &ph, const T *u, const T 
     hvp_fin<T, false>(c, ph, u, v, y, hp, s);
 }
 
-void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *lam, double *dLda,
-                      cudaStream_t s)
+void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
+                      double *dLda, cudaStream_t s)
 {
     c.n_launch += 1;
     const size_t sm = smem_verts(c, sizeof(double), 2);
     if (c.dim == 2)
-        k_tile_vjp<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, lam, dLda);
+        k_tile_vjp<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, a, lam, dLda);
     else
-        k_tile_vjp<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, lam, dLda);
+        k_tile_vjp<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, a, lam, dLda);
 }
 
 // Opt every kernel that may need more than 48 KB of dynamic shared memory into

@@ -83,6 +83,22 @@ __device__ __forceinline__ void log_terms(int mode, T mu, T lam, T J, T &l, T &c
     }
 }
 
+// Active-spring muscle psi = (k/2)(s/a - 1)^2 of q = F f, s = |q|
+// (Eq. active-spring-potential with s = l/l0): dpsi/dq = c1 q and
+// (d2psi/dq2) dq = c1 dq + c2 (q . dq) q with c1 = k (s/a - 1)/(a s) and
+// c2 = k/(a s^3).  A padding element (live = false) contributes nothing.
+template <typename T>
+__device__ __forceinline__ void spring_terms(bool live, T k, T a, T s, T &c1, T &c2)
+{
+    if (!live) {
+        c1 = c2 = T(0);
+        return;
+    }
+    const T ia = drcp(a), is = drcp(s);
+    c1 = k * (s * ia - T(1)) * ia * is;
+    c2 = k * ia * is * is * is;
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void load_B(const ElemDev<T> &ed, int64_t e, T B[D][D])
 {

@@ -80,6 +80,7 @@ struct Phys {
     int log_mode = 0;
     int dyn = 0;
     double s_el = 1.0;
+    int muscle = 0;              // 0: contractile (k/2) a |F f|^2; 1: active spring (k/2)(|F f|/a - 1)^2
     const double *fw = nullptr;  // [nv] 2 k_f ReLU(eps - y0), or null: no friction
     const double *u0 = nullptr;  // [nv][dim] displacement x0 - X of the step's start
 };
@@ -118,6 +119,7 @@ struct Ctx {
     ElemDev<double> e64;
     ElemDev<float> e32;
     int threads = 256;
+    int muscle = 0;              // muscle model (the spring's HVP also stages the fiber)
     double *partials = nullptr;  // [n_partials] FP64 block partial sums
     int n_fin_blocks = 1;
     DevScalars *sc = nullptr;
@@ -157,8 +159,8 @@ template <typename T>
 size_t hvp_smem(const Ctx &c);
 cudaError_t configure_elem_kernels();
 
-// dLda[perm[e]] = -s_el W k (F f).(dF(lam) f)
-void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *lam,
+// dLda[perm[e]] = -s_el W (d2psi_m/dq da).(dF(lam) f), q = F f; a in tile order
+void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
                       double *dLda, cudaStream_t s);
 
 // ---------------------------------------------------------------- vector kernels (vec_kernels.cu)

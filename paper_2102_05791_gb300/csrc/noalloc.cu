@@ -44,10 +44,11 @@ thread_local std::string g_noalloc_error;
 
 struct NoAllocMaterial {
     double mu, lam, k, rho, grav, kc;
-    int cpow, log_mode;
+    int cpow, log_mode, muscle;
 };
 
-// Energy of element e from rest and current positions: W (Psi + k/2 a |F f|^2)
+// Energy of element e from rest and current positions: W (Psi + psi_m), with
+// psi_m = k/2 a |F f|^2 (contractile) or k/2 (|F f|/a - 1)^2 (active spring),
 // plus the element's share of the gravity potential, rho W g / (dim+1) * sum y.
 template <int D>
 __device__ double element_energy(int64_t e, const double *X, const int32_t *T, const double *x, const double *a,
@@ -112,7 +113,12 @@ __device__ double element_energy(int64_t e, const double *X, const int32_t *T, c
     }
     double ysum = 0.0;
     for (int k = 0; k <= D; ++k) ysum += x[(int64_t)t[k] * D + 1];
-    return W * (0.5 * m.mu * (I1 - D) - m.mu * l + 0.5 * m.lam * l * l + 0.5 * m.k * a[e] * Ff2) +
+    double psim = 0.5 * m.k * a[e] * Ff2;
+    if (m.muscle) {
+        const double r = sqrt(Ff2) / a[e] - 1.0;
+        psim = 0.5 * m.k * r * r;
+    }
+    return W * (0.5 * m.mu * (I1 - D) - m.mu * l + 0.5 * m.lam * l * l + psim) +
            m.rho * W * m.grav / (D + 1) * ysum;
 }
 
@@ -183,6 +189,8 @@ extern "C" int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const
         return noalloc_fail(SIM_EINVAL, "contact_power must be 2 or 3");
     if (mat->log_mode != SIM_LOG_EXACT && mat->log_mode != SIM_LOG_QUAD)
         return noalloc_fail(SIM_EINVAL, "log_mode must be SIM_LOG_EXACT or SIM_LOG_QUAD");
+    if (mat->muscle_model != SIM_MUSCLE_CONTRACTILE && mat->muscle_model != SIM_MUSCLE_SPRING)
+        return noalloc_fail(SIM_EINVAL, "muscle_model must be SIM_MUSCLE_CONTRACTILE or SIM_MUSCLE_SPRING");
     NoAllocScratch *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != SIM_OK) return rc;
@@ -191,7 +199,7 @@ extern "C" int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const
     cudaError_t e = cudaMemsetAsync(&scratch->ticket, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return noalloc_fail(SIM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const NoAllocMaterial m{mat->mu, mat->lambda, mat->k_muscle, mat->density, mat->gravity, mat->k_contact,
-                            mat->contact_power, mat->log_mode};
+                            mat->contact_power, mat->log_mode, mat->muscle_model};
     const int64_t nmax = n_elem > n_vert ? n_elem : n_vert;
     const int grid = (int)((nmax + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
     if (dim == 2)

@@ -115,6 +115,7 @@ static Phys make_phys(const sim_handle *h, bool dyn)
     ph.kc = h->mat.k_contact;
     ph.cpow = h->mat.contact_power;
     ph.log_mode = h->mat.log_mode;
+    ph.muscle = h->mat.muscle_model;
     ph.dyn = dyn ? 1 : 0;
     ph.s_el = dyn ? h->mat.dt * h->mat.dt : 1.0;
     if (dyn && h->fw) {
@@ -358,6 +359,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if ((rc = upload(h, tb.fin_ptr, &td.fin_ptr))) return rc;
     if ((rc = upload(h, tb.vfin, &td.vfin))) return rc;
     c.threads = h->opt.threads > 0 ? h->opt.threads : (d == 3 ? 128 : 256);
+    c.muscle = h->mat.muscle_model;
     if (c.threads % 32 || c.threads > 256) return fail(h, SIM_EINVAL, "threads must be a multiple of 32, at most 256");
     c.n_fin_blocks = std::max(1, (td.n_fin + 255) / 256);
 
@@ -427,6 +429,8 @@ extern "C" int sim_create(const sim_mesh *mesh, const sim_material *mat, const s
         return fail(nullptr, SIM_EINVAL, "contact_power must be 2 or 3");
     if (mat->log_mode != SIM_LOG_EXACT && mat->log_mode != SIM_LOG_QUAD)
         return fail(nullptr, SIM_EINVAL, "log_mode must be SIM_LOG_EXACT or SIM_LOG_QUAD");
+    if (mat->muscle_model != SIM_MUSCLE_CONTRACTILE && mat->muscle_model != SIM_MUSCLE_SPRING)
+        return fail(nullptr, SIM_EINVAL, "muscle_model must be SIM_MUSCLE_CONTRACTILE or SIM_MUSCLE_SPRING");
     if (!(mat->dt >= 0.0) || !std::isfinite(mat->mu) || !std::isfinite(mat->lambda) || !std::isfinite(mat->k_muscle) ||
         !std::isfinite(mat->density) || !std::isfinite(mat->gravity) || !std::isfinite(mat->k_contact))
         return fail(nullptr, SIM_EINVAL, "bad material scalar");
@@ -818,15 +822,17 @@ extern "C" int sim_adjoint_solve(sim_handle *h, const double *x_star, const doub
     return status;
 }
 
-extern "C" int sim_param_vjp(sim_handle *h, const double *x_star, const double *lambda, double *dLda, void *stream)
+extern "C" int sim_param_vjp(sim_handle *h, const double *x_star, const double *a, const double *lambda,
+                             double *dLda, void *stream)
 {
     CHECK_H(h);
-    if (!x_star || !lambda || !dLda) return fail(h, SIM_EINVAL, "null argument");
+    if (!x_star || !a || !lambda || !dLda) return fail(h, SIM_EINVAL, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     if ((rc = set_state(h, x_star, false, s))) return rc;
+    if ((rc = set_activation(h, a, s))) return rc;
     const Phys ph = make_phys(h, h->mat.dt > 0.0);
-    launch_param_vjp(h->ctx, ph, h->u, lambda, dLda, s);
+    launch_param_vjp(h->ctx, ph, h->u, h->a64, lambda, dLda, s);
     CKL(h);
     return SIM_OK;
 }
@@ -866,7 +872,7 @@ extern "C" int sim_step_backward(sim_handle *h, const double *x0, const double *
     if (rc != SIM_OK) return rc;
     launch_step_bwd_combine(h->ctx, h->lam, vbar1, dt, h->fw, h->mat.k_friction, x0, x1, xbar0, vbar0, s);
     CKL(h);
-    return sim_param_vjp(h, x1, h->lam, abar, stream);
+    return sim_param_vjp(h, x1, a, h->lam, abar, stream);
 }
 
 static int ensure_rollout_buffers(sim_handle *h)

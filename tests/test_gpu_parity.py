@@ -104,7 +104,7 @@ def test_param_vjp_fp64(prob):
     x = deformed(prob, 0.03, seed=7)
     lam = np.random.default_rng(8).standard_normal(x.shape)
     lam[prob.fixed.astype(bool)] = 0.0
-    out = host(sim.param_vjp(dev(x), dev(lam)))
+    out = host(sim.param_vjp(dev(x), dev(prob.a), dev(lam)))
     ref = m.param_vjp(x, lam)
     assert np.abs(out - ref).max() <= TOL64 * np.abs(ref).max()
 
@@ -134,7 +134,7 @@ def test_quasistatic_solve_and_gradient_c1(precision):
     # adjoint + parameter VJP
     gL = oracle.mean_loss_grad(xg, p.target)
     lam, st_a = sim.adjoint(x, dev(p.a), dev(gL))
-    dLda = host(sim.param_vjp(x, lam))
+    dLda = host(sim.param_vjp(x, dev(p.a), lam))
     _, _, dLda_or, _ = oracle.quasistatic_forward_backward(m, p.a, p.target, rtol=1e-10)
     err = np.linalg.norm(dLda - dLda_or) / np.linalg.norm(dLda_or)
     assert err <= (1e-7 if precision == "fp64" else 1e-4), err
@@ -147,7 +147,7 @@ def test_quasistatic_solve_and_gradient_3d(precision):
                                          adjoint_rtol=1e-10 if precision == "fp64" else 1e-6)
     gL = oracle.mean_loss_grad(xg, p.target)
     lam, _ = sim.adjoint(x, dev(p.a), dev(gL))
-    dLda = host(sim.param_vjp(x, lam))
+    dLda = host(sim.param_vjp(x, dev(p.a), lam))
     _, _, dLda_or, _ = oracle.quasistatic_forward_backward(m, p.a, p.target, rtol=1e-10)
     err = np.linalg.norm(dLda - dLda_or) / np.linalg.norm(dLda_or)
     assert err <= (1e-7 if precision == "fp64" else 1e-4), err
@@ -167,7 +167,7 @@ def test_config3_full_size_properties():
     b[p.fixed.astype(bool)] = 0.0
     res = np.linalg.norm(m.hvp(xg, p.a, lg) - b) / np.linalg.norm(b)
     assert res <= 1e-4, res
-    dLda = host(sim.param_vjp(x, lam))
+    dLda = host(sim.param_vjp(x, dev(p.a), lam))
     ref = m.param_vjp(xg, lg)
     assert np.abs(dLda - ref).max() <= TOL64 * np.abs(ref).max()
 

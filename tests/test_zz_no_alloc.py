@@ -23,17 +23,23 @@ TOL64 = 1e-12
 
 def _material(p):
     from paper_2102_05791_gb300 import _lib
-    return _lib.SimMaterial(p.mu, p.lam, p.k_muscle, p.density, p.gravity, p.k_contact, p.contact_power,
-                            p.log_mode, 0.0, None)
+    mat = _lib.SimMaterial(p.mu, p.lam, p.k_muscle, p.density, p.gravity, p.k_contact, p.contact_power,
+                           p.log_mode, 0.0, None)
+    mat.muscle_model = p.muscle_model
+    return mat
 
 
+@pytest.mark.parametrize("muscle", [0, 1], ids=["contractile", "spring"])
 @pytest.mark.parametrize("name", ["c1", "small3d"])
-def test_energy_noalloc_matches_handle_energy_twice(name):
+def test_energy_noalloc_matches_handle_energy_twice(name, muscle):
     from paper_2102_05791_gb300 import _lib
     L = _lib.load()
     p = synth.make_config1() if name == "c1" else synth.make_small3d(6, 4, 4, split=6, seed=51)
     p.k_contact = 1e5
-    sim = make_sim(p, "fp64")
+    p.muscle_model = muscle
+    if muscle:
+        p.a = 0.5 + 0.5 * p.a  # the spring needs a > 0
+    sim = make_sim(p, "fp64", muscle_model=muscle)
     mat = _material(p)
     X, T = dev(p.X), torch.from_numpy(p.T).cuda().contiguous()
     fiber, a = dev(p.fiber), dev(p.a)
