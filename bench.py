@@ -341,7 +341,7 @@ def run_ours(args, rank, world, local_rank):
     def step(x_init=None, a_in=None):
         x, st = sim.solve(a if a_in is None else a_in, x_init=x_init)
         lam, sta = sim.adjoint(x, a if a_in is None else a_in, loss_grad(x))
-        g = sim.param_vjp(x, lam)
+        g = sim.param_vjp(x, a if a_in is None else a_in, lam)
         return x, g, st["cg_iters_total"] + sta["cg_iters_total"], st, sta
 
     def barrier():
