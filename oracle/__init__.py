@@ -77,6 +77,7 @@ def lib():
         L.or_grad.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
         L.or_hvp.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
         L.or_param_vjp.argtypes = [C.POINTER(_Model), dp, dp, dp, dp]
+        L.or_material_vjp.argtypes = [C.POINTER(_Model), dp, dp, dp, dp, dp, dp]
         L.or_cg.argtypes = [C.POINTER(_Model), dp, dp, dp, dp, C.c_double, C.c_int, dp]
         L.or_cg.restype = C.c_int
         L.or_newton.argtypes = [C.POINTER(_Model), dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
@@ -181,6 +182,13 @@ class Model:
         out = np.zeros(self.ne)
         lib().or_param_vjp(C.byref(self._c()), _p(x), _p(a), _p(lam), _p(out))
         return out
+
+    def material_vjp(self, x, lam, a):
+        """Per-element (dL/dmu, dL/dlambda, dL/dk) at x for adjoint lam."""
+        x, lam, a = _f64(x), _f64(lam), _f64(a)
+        out = [np.zeros(self.ne) for _ in range(3)]
+        lib().or_material_vjp(C.byref(self._c()), _p(x), _p(a), _p(lam), *[_p(o) for o in out])
+        return tuple(out)
 
     # -- solvers ---------------------------------------------------------------
     def cg(self, x, a, b, rtol=1e-10, max_iter=10000):

@@ -605,6 +605,54 @@ void or_param_vjp(const or_model *M, const double *x, const double *a, const dou
     }
 }
 
+/* ---------------------------------------------------------------- material VJP */
+
+/* dL/dtheta_e = -s lambda^T d(grad E)/dtheta_e for theta = mu, lambda and the
+ * muscle stiffness k of element e (Eq. dLda-re-ordered with theta in place
+ * of a).  P is linear in (mu, lambda) and the muscle force linear in k, so
+ * each derivative of P is P itself evaluated with that parameter set to 1
+ * and the others to 0.  Any output may be NULL. */
+void or_material_vjp(const or_model *M, const double *x, const double *a, const double *lam, double *dmu,
+                     double *dlam, double *dk)
+{
+    int d = M->d;
+    double s = M->h > 0.0 ? M->h * M->h : 1.0;
+    or_model Mmu = *M, Mlam = *M, Mk = *M;
+    Mmu.mu = 1.0;
+    Mmu.lam = 0.0;
+    Mlam.mu = 0.0;
+    Mlam.lam = 1.0;
+    Mk.k_muscle = 1.0;
+    for (long e = 0; e < M->ne; ++e) {
+        double Ds[3][3], dDs[3][3], B[3][3], F[3][3], dF[3][3], P[3][3];
+        edge_matrix(M, e, x, Ds);
+        edge_matrix(M, e, lam, dDs);
+        load_Dminv(M, e, B);
+        mul_d(d, Ds, B, F);
+        mul_d(d, dDs, B, dF);
+        if (dmu) {
+            pk1(&Mmu, F, P);
+            dmu[e] = -s * M->W[e] * ddot_d(d, P, dF);
+        }
+        if (dlam) {
+            pk1(&Mlam, F, P);
+            dlam[e] = -s * M->W[e] * ddot_d(d, P, dF);
+        }
+        if (dk) {
+            const double *f = M->fiber + e * d;
+            double q[3] = {0, 0, 0}, dq[3] = {0, 0, 0}, dpsi[3], t = 0.0;
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    q[i] += F[i][j] * f[j];
+                    dq[i] += dF[i][j] * f[j];
+                }
+            muscle_dpsi(&Mk, a[e], q, dpsi);
+            for (int i = 0; i < d; ++i) t += dpsi[i] * dq[i];
+            dk[e] = -s * M->W[e] * t;
+        }
+    }
+}
+
 /* ---------------------------------------------------------------- solvers */
 
 static double vdot(long n, const double *a, const double *b)
