@@ -190,6 +190,18 @@ int sim_adjoint_solve(sim_handle *h, const double *x_star, const double *a, cons
 int sim_param_vjp(sim_handle *h, const double *x_star, const double *a, const double *lambda,
                   double *dLda, void *stream);
 
+/* Material-parameter VJPs per element (Eq. dLda-re-ordered with a material
+ * parameter theta in place of a): dL/dtheta_e = -s lambda^T d(grad E)/dtheta_e
+ * = -s W_e (dP_e/dtheta) : dF_e(lambda) for theta = mu, lambda, with
+ * dP/dmu = F - l'(J) cof F and dP/dlambda = l(J) l'(J) cof F (l the exact or
+ * quadratic log), and -s W_e (d2psi_m/dq dk) . (dF_e(lambda) f_e) for the
+ * muscle stiffness k.  The derivative for a global parameter (or one mesh's)
+ * is the sum over elements.  x_star, a, lambda as for sim_param_vjp; each
+ * output is a DEVICE [n_elem] double array in the caller's element order, or
+ * NULL to skip it. */
+int sim_material_vjp(sim_handle *h, const double *x_star, const double *a, const double *lambda,
+                     double *dLdmu, double *dLdlambda, double *dLdk, void *stream);
+
 /* One backward-Euler step (Eq. opt-be), dt > 0 only: x1 = argmin of the
  * incremental potential started from x0, v1 = (x1 - x0)/dt.  x1 and v1 must
  * not alias x0 or v0. */
@@ -284,12 +296,16 @@ int sim_batch_sizes(const sim_batch *b, int *n_meshes, int64_t *total_vert, int6
  *   abar_seq [n_steps][E] receives dL/da_t; xbar0, vbar0 [V][d] receive
  *     dL/dx_0, dL/dv_0;
  *   mesh_stats [n_meshes][4] ints (or NULL): status, Newton iterations, CG
- *     iterations forward, CG iterations adjoint.
+ *     iterations forward, CG iterations adjoint;
+ *   mat_grad [n_meshes][3] doubles (or NULL): dL/dmu_m, dL/dlambda_m and
+ *     dL/dk of mesh m, summed over its elements and steps (the material VJP
+ *     of sim_material_vjp at each step's lambda, dt^2-scaled); for the shared
+ *     k the batch's derivative is the sum over meshes.
  * Stream-ordered; returns after enqueueing (synchronise before reading). */
 int sim_batch_rollout(sim_batch *b, int n_steps, double *states_x, double *states_v,
                       const double *a_seq, const double *xbarT, const double *vbarT,
                       double *abar_seq, double *xbar0, double *vbar0, int *mesh_stats,
-                      void *stream);
+                      double *mat_grad, void *stream);
 
 /* Energy without allocation.  The paper has no counterpart: this is a
  * deployment aid.  Returns in E_out (one device double) the quasistatic

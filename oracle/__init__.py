@@ -294,7 +294,7 @@ def be_step(model: Model, x0, v0, a, rtol=1e-8, max_newton=100):
     return x1, v1, st
 
 
-def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12):
+def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12, material=False):
     """Adjoint of one backward-Euler step.
 
     Optimality M (x1 - xhat) + h^2 grad E(x1) = 0 with xhat = x0 + h v0 gives
@@ -302,6 +302,8 @@ def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12):
     lambda = (M + h^2 H)^-1 (xbar1 + vbar1/h):
       xbar0 = M lambda - vbar1/h,  vbar0 = h M lambda,
       abar  = -h^2 lambda^T d2E/dx da.
+    With material, also returns the step's (dL/dmu, dL/dlambda, dL/dk) summed
+    over the elements (-h^2 lambda^T d2E/dx dtheta).
     """
     h = model.h
     m = model.replace(xhat=_f64(x0 + h * v0), x0=_f64(x0))
@@ -326,6 +328,8 @@ def be_step_backward(model: Model, x0, v0, x1, a, xbar1, vbar1, adj_rtol=1e-12):
         xbar0[fx] = 0.0
         vbar0[fx] = 0.0
     abar = m.param_vjp(x1, lam, a)
+    if material:
+        return xbar0, vbar0, abar, np.array([v.sum() for v in m.material_vjp(x1, lam, a)])
     return xbar0, vbar0, abar
 
 
@@ -341,13 +345,20 @@ def rollout(model: Model, x0, v0, a_seq, rtol=1e-8):
     return xs, vs
 
 
-def rollout_backward(model: Model, xs, vs, a_seq, xbarT, vbarT, adj_rtol=1e-12):
-    """Backpropagation through time over a fully stored rollout."""
+def rollout_backward(model: Model, xs, vs, a_seq, xbarT, vbarT, adj_rtol=1e-12, material=False):
+    """Backpropagation through time over a fully stored rollout.  With
+    material, also returns (dL/dmu, dL/dlambda, dL/dk) summed over steps."""
     xbar, vbar = _f64(xbarT), _f64(vbarT)
     abars = [None] * len(a_seq)
+    mat = np.zeros(3)
     for t in reversed(range(len(a_seq))):
-        xbar, vbar, abars[t] = be_step_backward(model, xs[t], vs[t], xs[t + 1], a_seq[t], xbar, vbar,
-                                                adj_rtol=adj_rtol)
+        out = be_step_backward(model, xs[t], vs[t], xs[t + 1], a_seq[t], xbar, vbar, adj_rtol=adj_rtol,
+                               material=material)
+        xbar, vbar, abars[t] = out[:3]
+        if material:
+            mat += out[3]
+    if material:
+        return xbar, vbar, np.stack(abars), mat
     return xbar, vbar, np.stack(abars)
 
 

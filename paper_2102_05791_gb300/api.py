@@ -140,6 +140,14 @@ class Simulator:
         self._check("sim_hvp", self._lib.sim_hvp(self._h, _ptr(x), _ptr(a), _ptr(v), _ptr(out), _stream()))
         return out
 
+    def material_vjp(self, x_star, a, lam):
+        """Per-element (dL/dmu, dL/dlambda, dL/dk) for adjoint lam at x_star."""
+        x_star, a, lam = self._vec(x_star), self._elem(a), self._vec(lam, name="lambda")
+        outs = [torch.empty(self.n_elem, dtype=torch.float64, device=self.device) for _ in range(3)]
+        self._check("sim_material_vjp", self._lib.sim_material_vjp(
+            self._h, _ptr(x_star), _ptr(a), _ptr(lam), *[_ptr(o) for o in outs], _stream()))
+        return tuple(outs)
+
     def param_vjp(self, x_star, a, lam):
         x_star, a, lam = self._vec(x_star), self._elem(a), self._vec(lam, name="lambda")
         out = torch.empty(self.n_elem, dtype=torch.float64, device=self.device)
@@ -303,9 +311,10 @@ class Batch:
         except Exception:
             pass
 
-    def rollout(self, x0, v0, a_seq, xbarT, vbarT, states=None):
+    def rollout(self, x0, v0, a_seq, xbarT, vbarT, states=None, material_grad=False):
         """Forward rollout + BPTT of every mesh.  Returns (states_x, states_v,
-        abar_seq, xbar0, vbar0, mesh_stats) as device tensors."""
+        abar_seq, xbar0, vbar0, mesh_stats) as device tensors, plus, with
+        material_grad, the [n_meshes, 3] per-mesh (dL/dmu, dL/dlambda, dL/dk)."""
         n_steps = int(a_seq.shape[0])
         if states is None:
             sx = torch.empty((n_steps + 1, self.V, self.dim), dtype=torch.float64, device=self.device)
@@ -319,12 +328,13 @@ class Batch:
         xb0 = torch.empty((self.V, self.dim), dtype=torch.float64, device=self.device)
         vb0 = torch.empty_like(xb0)
         ms = torch.zeros((self.n_meshes, 4), dtype=torch.int32, device=self.device)
+        mg = torch.empty((self.n_meshes, 3), dtype=torch.float64, device=self.device) if material_grad else None
         rc = self._lib.sim_batch_rollout(self._h, n_steps, _ptr(sx), _ptr(sv), _ptr(a_seq),
                                          _ptr(xbarT.contiguous()), _ptr(vbarT.contiguous()), _ptr(abar), _ptr(xb0),
-                                         _ptr(vb0), _ptr(ms), _stream())
+                                         _ptr(vb0), _ptr(ms), None if mg is None else _ptr(mg), _stream())
         if rc != 0:
             raise SimError("sim_batch_rollout", rc, self._lib.sim_batch_last_error(self._h).decode())
-        return sx, sv, abar, xb0, vb0, ms
+        return (sx, sv, abar, xb0, vb0, ms, mg) if material_grad else (sx, sv, abar, xb0, vb0, ms)
 
 
 # ---------------------------------------------------------------- autograd

@@ -61,6 +61,7 @@ struct BatchDev {
     double *c64 = nullptr;
     int *counter = nullptr;
     int *mstat = nullptr;   // [M][4]: status, newton iters, cg iters fwd, cg iters adj
+    double *mgrad = nullptr;  // [M][3]: dL/dmu, dL/dlambda, dL/dk of each mesh over the rollout
 };
 
 struct Mesh {
@@ -556,7 +557,7 @@ __device__ int step_forward(const BatchDev &b, const Mesh &m, const double *x0, 
 // vbar <- h M lambda, abar_t = -h^2 lambda^T d2E/dx da.
 template <int D>
 __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0, const double *x1, const double *a_t,
-                             double *abar_t, int *cg_it, double *red)
+                             double *abar_t, int *cg_it, double mat[3], double *red)
 {
     const int64_t o = m.v0 * D, n = (int64_t)m.nv * D;
     const double h = b.dt;
@@ -629,16 +630,40 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
         }
         if (fv > 0.0 && !fx) b.xbar[v * D + 1] += 2.0 * b.kf * ysum;
     }
-    // parameter VJP at x1
+    // parameter VJP at x1, and this step's material VJPs summed over the mesh:
+    // -h^2 W (dP/dtheta) : dF(lambda), dP/dmu = F - l' cof F, dP/dlambda = l l' cof F
+    double tmu = 0.0, tlam = 0.0, tk = 0.0;
     for (int le = threadIdx.x; le < m.ne; le += blockDim.x) {
         const int64_t e = m.e0 + le;
         int lid[D + 1];
         elem_ids<D>(b, e, lid);
-        double B[D][D], gv[D], W, f[D], Du[D][D], Dl[D][D], F[D][D];
+        double B[D][D], gv[D], W, f[D], Du[D][D], Dl[D][D], F[D][D], dF[D][D], C[D][D];
         load_elem<double, D>(b.e64, b.estride, e, B, gv, W, f);
         edge_of<double, double, D>(b.u, m, lid, Du);
         edge_of<double, double, D>(b.lacc, m, lid, Dl);
         mul<double, D>(Du, B, F, true);
+        mul<double, D>(Dl, B, dF, false);
+        cof<double, D>(F, C);
+        const double J = detF<double, D>(F, C);
+        double FdF = 0.0, CdF = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                FdF += F[i][j] * dF[i][j];
+                CdF += C[i][j] * dF[i][j];
+            }
+        double l, lp;
+        if (b.log_mode == 0) {
+            l = log(J);
+            lp = 1.0 / J;
+        } else {
+            l = (J - 1.0) - 0.5 * (J - 1.0) * (J - 1.0);
+            lp = 2.0 - J;
+        }
+        const double sW = -h * h * W;
+        tmu += sW * (FdF - lp * CdF);
+        tlam += sW * l * lp * CdF;
         double dot = 0.0, s2 = 0.0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -651,13 +676,19 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
             dot += Ff * dFf;
             s2 += Ff * Ff;
         }
-        double kq = b.k;  // d2psi_m/dq da = kq q
+        double kq = b.k;                  // d2psi_m/dq da = kq q
+        double ck = a_t[e];               // d2psi_m/dq dk = ck q
         if (b.muscle) {
             const double s = sqrt(s2), ia = 1.0 / a_t[e];
             kq = b.k * (ia * ia - 2.0 * s * ia * ia * ia) / s;
+            ck = (s * ia - 1.0) * ia / s;
         }
         abar_t[e] = -h * h * W * kq * dot;
+        tk += sW * ck * dot;
     }
+    mat[0] += bsum(tmu, red);
+    mat[1] += bsum(tlam, red);
+    mat[2] += bsum(tk, red);
     __syncthreads();
     return status;
 }
@@ -697,12 +728,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
             b.vbar[o + i] = vbarT[o + i];
         }
         __syncthreads();
+        double mat[3] = {0.0, 0.0, 0.0};
         for (int t = n_steps - 1; t >= 0; --t) {
             const int st = step_backward<D>(b, m, xs + t * VD, xs + (t + 1) * VD, a_seq + (size_t)t * E,
-                                            abar_seq + (size_t)t * E, &cg_a, red);
+                                            abar_seq + (size_t)t * E, &cg_a, mat, red);
             if (st != SIM_OK && status == SIM_OK) status = st;
         }
         if (threadIdx.x == 0) {
+            b.mgrad[3 * mi + 0] = mat[0];
+            b.mgrad[3 * mi + 1] = mat[1];
+            b.mgrad[3 * mi + 2] = mat[2];
             b.mstat[4 * mi + 0] = status;
             b.mstat[4 * mi + 1] = newton_it;
             b.mstat[4 * mi + 2] = cg_f;
@@ -949,9 +984,10 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.c64 = balloc<double>(bt, (size_t)E * nc * d);
     b.counter = balloc<int>(bt, 1);
     b.mstat = balloc<int>(bt, (size_t)4 * M);
+    b.mgrad = balloc<double>(bt, (size_t)3 * M);
     const void *ptrs[] = {b.voff, b.eoff, b.order, b.X, b.mass, b.fixed, b.conn, b.vinc_ptr, b.vinc, b.e32, b.e64,
                           b.mu, b.lam, b.u, b.uhat, b.g, b.w64, b.r64, b.Hx, b.lacc, b.xbar, b.vbar, b.u32,
-                          b.d, b.r, b.p, b.Ap, b.c32, b.c64, b.counter, b.mstat};
+                          b.d, b.r, b.p, b.Ap, b.c32, b.c64, b.counter, b.mstat, b.mgrad};
     for (const void *p : ptrs)
         if (!p) return bfail(bt, SIM_ENOMEM, "device allocation or upload failed");
     if (b.kf > 0.0 && (!b.fw || !b.u0)) return bfail(bt, SIM_ENOMEM, "device allocation failed");
@@ -986,7 +1022,7 @@ extern "C" int sim_batch_sizes(const sim_batch *b, int *n_meshes, int64_t *total
 
 extern "C" int sim_batch_rollout(sim_batch *bt, int n_steps, double *states_x, double *states_v, const double *a_seq,
                                  const double *xbarT, const double *vbarT, double *abar_seq, double *xbar0,
-                                 double *vbar0, int *mesh_stats, void *stream)
+                                 double *vbar0, int *mesh_stats, double *mat_grad, void *stream)
 {
     if (!bt) return SIM_EINVAL;
     if (n_steps <= 0 || !states_x || !states_v || !a_seq || !xbarT || !vbarT || !abar_seq || !xbar0 || !vbar0)
@@ -1038,5 +1074,6 @@ extern "C" int sim_batch_rollout(sim_batch *bt, int n_steps, double *states_x, d
     BCK(bt, cudaMemcpyAsync(xbar0, b.xbar, VD * sizeof(double), cudaMemcpyDeviceToDevice, s));
     BCK(bt, cudaMemcpyAsync(vbar0, b.vbar, VD * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (mesh_stats) BCK(bt, cudaMemcpyAsync(mesh_stats, b.mstat, sizeof(int) * 4 * bt->M, cudaMemcpyDeviceToDevice, s));
+    if (mat_grad) BCK(bt, cudaMemcpyAsync(mat_grad, b.mgrad, sizeof(double) * 3 * bt->M, cudaMemcpyDeviceToDevice, s));
     return SIM_OK;
 }

@@ -732,6 +732,87 @@ __global__ void __launch_bounds__(256) k_tile_vjp(TileDev td, ElemDev<double> ed
     }
 }
 
+// Material-parameter VJPs per element: -s W (dP/dtheta) : dF(lam) with
+// dP/dmu = F - l'(J) cof F, dP/dlambda = l(J) l'(J) cof F, and for the
+// muscle stiffness -s W (d2psi_m/dq dk) . dq(lam).  Null outputs are skipped.
+template <int D>
+__global__ void __launch_bounds__(256) k_tile_mat_vjp(TileDev td, ElemDev<double> ed, VertDev vd, Phys ph,
+                                                      const double *__restrict__ u, const double *__restrict__ a,
+                                                      const double *__restrict__ lam, double *__restrict__ dmu,
+                                                      double *__restrict__ dlam, double *__restrict__ dk)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *su = reinterpret_cast<double *>(smem);
+    double *sl = su + td.max_tv * D;
+    const int t = blockIdx.x;
+    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
+    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
+        const int64_t gid = td.lv_gid[vs + k];
+        const bool fx = vd.fixed[gid] != 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            su[k * D + c] = u[gid * D + c];
+            sl[k * D + c] = fx ? 0.0 : lam[gid * D + c];
+        }
+    }
+    __syncthreads();
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
+        const int64_t e = es + le;
+        const int32_t pe = td.perm[e];
+        if (pe < 0) continue;  // padding
+        int lid[D + 1];
+        unpack<D>(td.conn[e], lid);
+        double B[D][D], Du[D][D], Dl[D][D], F[D][D], dF[D][D], C[D][D];
+        load_B<double, D>(ed, e, B);
+        edges<double, D>(su, lid, Du);
+        edges<double, D>(sl, lid, Dl);
+        mul<double, D>(Du, B, F, true);
+        mul<double, D>(Dl, B, dF, false);
+        cof<double, D>(F, C);
+        const double J = detF<double, D>(F, C);
+        double FdF = 0.0, CdF = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                FdF += F[i][j] * dF[i][j];
+                CdF += C[i][j] * dF[i][j];
+            }
+        double l, lp;  // l(J) and l'(J)
+        if (ph.log_mode == 0) {
+            l = log(J);
+            lp = 1.0 / J;
+        } else {
+            l = (J - 1.0) - 0.5 * (J - 1.0) * (J - 1.0);
+            lp = 2.0 - J;
+        }
+        const double sW = -ph.s_el * __ldg(ed.field(FI<D>::W) + e);
+        if (dmu) dmu[pe] = sW * (FdF - lp * CdF);
+        if (dlam) dlam[pe] = sW * l * lp * CdF;
+        if (dk) {
+            double qdq = 0.0, s2 = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double q = 0.0, dq = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    q += F[i][k] * __ldg(ed.field(FI<D>::F + k) + e);
+                    dq += Dl[i][k] * __ldg(ed.field(FI<D>::G + k) + e);  // dF(lam) f = Dlam g
+                }
+                qdq += q * dq;
+                s2 += q * q;
+            }
+            double c = a[e];  // d2psi_m/dq dk = c q
+            if (ph.muscle) {
+                const double sq = sqrt(s2);
+                c = (sq / a[e] - 1.0) / (a[e] * sq);
+            }
+            dk[pe] = sW * c * qdq;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 static inline size_t smem_verts(const Ctx &c, size_t elt, int nfields)
@@ -882,6 +963,17 @@ void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const doubl
         k_tile_vjp<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, a, lam, dLda);
 }
 
+void launch_material_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
+                         double *dmu, double *dlam, double *dk, cudaStream_t s)
+{
+    c.n_launch += 1;
+    const size_t sm = smem_verts(c, sizeof(double), 2);
+    if (c.dim == 2)
+        k_tile_mat_vjp<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, a, lam, dmu, dlam, dk);
+    else
+        k_tile_mat_vjp<3><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, a, lam, dmu, dlam, dk);
+}
+
 // Opt every kernel that may need more than 48 KB of dynamic shared memory into
 // the larger carve-out.
 cudaError_t configure_elem_kernels()
@@ -910,6 +1002,8 @@ cudaError_t configure_elem_kernels()
 #undef SET_HVP
     SET((k_tile_vjp<2>));
     SET((k_tile_vjp<3>));
+    SET((k_tile_mat_vjp<2>));
+    SET((k_tile_mat_vjp<3>));
 #undef SET
     return e;
 }

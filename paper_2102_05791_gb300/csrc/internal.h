@@ -162,6 +162,9 @@ cudaError_t configure_elem_kernels();
 // dLda[perm[e]] = -s_el W (d2psi_m/dq da).(dF(lam) f), q = F f; a in tile order
 void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
                       double *dLda, cudaStream_t s);
+// per-element dL/dmu, dL/dlambda, dL/dk (caller order; null outputs skipped)
+void launch_material_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
+                         double *dmu, double *dlam, double *dk, cudaStream_t s);
 
 // ---------------------------------------------------------------- vector kernels (vec_kernels.cu)
 template <typename T>

@@ -837,6 +837,22 @@ extern "C" int sim_param_vjp(sim_handle *h, const double *x_star, const double *
     return SIM_OK;
 }
 
+extern "C" int sim_material_vjp(sim_handle *h, const double *x_star, const double *a, const double *lambda,
+                                double *dLdmu, double *dLdlambda, double *dLdk, void *stream)
+{
+    CHECK_H(h);
+    if (!x_star || !a || !lambda) return fail(h, SIM_EINVAL, "null argument");
+    if (!dLdmu && !dLdlambda && !dLdk) return SIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = set_state(h, x_star, false, s))) return rc;
+    if ((rc = set_activation(h, a, s))) return rc;
+    const Phys ph = make_phys(h, h->mat.dt > 0.0);
+    launch_material_vjp(h->ctx, ph, h->u, h->a64, lambda, dLdmu, dLdlambda, dLdk, s);
+    CKL(h);
+    return SIM_OK;
+}
+
 extern "C" int sim_step_forward(sim_handle *h, const double *x0, const double *v0, const double *a, double *x1,
                                 double *v1, sim_solve_stats *st, void *stream)
 {

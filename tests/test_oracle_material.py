@@ -112,3 +112,26 @@ def test_be_step_material_gradient_matches_fd():
         xm, _, _ = oracle.be_step(m.replace(**{name: th - eps}), x0, v0, p.a, rtol=1e-13)
         fd = np.sum(c * (xp - xm)) / (2 * eps)
         assert math.isclose(fd, v.sum(), rel_tol=1e-5), name
+
+
+def test_rollout_material_gradient_matches_fd():
+    """BPTT material gradient of a 3-step rollout (sum over steps of the
+    per-step material VJPs) vs central FD of the rollout's loss."""
+    p = synth.make_small2d(4, 2, fix_bottom=False)
+    p.k_contact, p.contact_power, p.dt = 1e6, 3, 1.0 / 30.0
+    p.k_friction = 2e3
+    m = oracle.make_model(p)
+    rng = np.random.default_rng(63)
+    a_seq = rng.uniform(0.0, 1.0, size=(3, p.n_elem))
+    x0 = p.X.copy()
+    v0 = 0.2 * rng.standard_normal(x0.shape)
+    c = rng.standard_normal(x0.shape)
+    xs, vs = oracle.rollout(m, x0, v0, a_seq, rtol=1e-13)
+    _, _, _, mat = oracle.rollout_backward(m, xs, vs, a_seq, c, np.zeros_like(c), material=True)
+    for name, v in zip(("mu", "lam", "k_muscle"), mat):
+        th = getattr(m, name)
+        eps = 1e-5 * th
+        xp, _ = oracle.rollout(m.replace(**{name: th + eps}), x0, v0, a_seq, rtol=1e-13)
+        xm, _ = oracle.rollout(m.replace(**{name: th - eps}), x0, v0, a_seq, rtol=1e-13)
+        fd = np.sum(c * (xp[-1] - xm[-1])) / (2 * eps)
+        assert math.isclose(fd, v, rel_tol=1e-5), name
