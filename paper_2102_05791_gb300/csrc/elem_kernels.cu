@@ -400,7 +400,9 @@ struct HvpSmem {
 // shared memory, the per-corner forces overwrite the element fields in place
 // (the corner array needs (D+1)*D <= NF columns per element), and one thread
 // per local vertex adds its corners in fixed order.
-template <typename T, int D, bool CG, int MINB, int MTE>
+// SPRING selects the active-spring muscle at compile time, so the
+// contractile kernel carries none of its code or its extra fields.
+template <typename T, int D, bool CG, int MINB, int MTE, bool SPRING>
 __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
                                                   const T *__restrict__ u, const T *__restrict__ a,
                                                   const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     extern __shared__ __align__(128) unsigned char smem[];
     // MTE != 0: the tile capacity is a compile-time constant, so every
     // element-field and corner offset below folds into an immediate
-    const int NF = ph.muscle ? HvpSmem<T, D>::NF_SPRING : HvpSmem<T, D>::NF;
+    constexpr int NF = SPRING ? HvpSmem<T, D>::NF_SPRING : HvpSmem<T, D>::NF;
     const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv, NF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
     T *sE = reinterpret_cast<T *>(smem + L.e);
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
             dvg[i] = s;
         }
-        if (ph.muscle) {  // spring, with q = F f = f + Du g
+        if constexpr (SPRING) {  // spring, with q = F f = f + Du g
             T q[D], s2 = T(0), qdq = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
@@ -882,12 +884,15 @@ template <typename T, int D, bool CG, int MINB>
 static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
     constexpr int CAP = D == 2 ? kCap2 : kCap3;
-    if (sizeof(T) == 4 && c.td.max_te == CAP)
-        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0)>, dim3(c.td.n_tiles), dim3(c.threads),
-                 hvp_smem<T>(c), s, c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+    if (c.muscle)  // the spring variant exists for the runtime tile capacity only
+        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0, true>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s,
+                 c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+    else if (sizeof(T) == 4 && c.td.max_te == CAP)
+        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0), false>, dim3(c.td.n_tiles),
+                 dim3(c.threads), hvp_smem<T>(c), s, c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
     else
-        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s, c.td,
-                 edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+        launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0, false>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s,
+                 c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
 }
 
 template <typename T, bool CG>
@@ -986,15 +991,19 @@ cudaError_t configure_elem_kernels()
     SET((k_tile_energy<3>));
     SET((k_tile_grad<2>));
     SET((k_tile_grad<3>));
-#define SET_HVP(T, MB)                                  \
-    SET((k_tile_hvp<T, 2, true, MB, 0>));               \
-    SET((k_tile_hvp<T, 3, true, MB, 0>));               \
-    SET((k_tile_hvp<T, 2, false, MB, 0>));              \
-    SET((k_tile_hvp<T, 3, false, MB, 0>));              \
-    SET((k_tile_hvp<T, 2, true, MB, (sizeof(T) == 4 ? kCap2 : 0)>));  \
-    SET((k_tile_hvp<T, 3, true, MB, (sizeof(T) == 4 ? kCap3 : 0)>));  \
-    SET((k_tile_hvp<T, 2, false, MB, (sizeof(T) == 4 ? kCap2 : 0)>)); \
-    SET((k_tile_hvp<T, 3, false, MB, (sizeof(T) == 4 ? kCap3 : 0)>));
+#define SET_HVP(T, MB)                                                       \
+    SET((k_tile_hvp<T, 2, true, MB, 0, false>));                             \
+    SET((k_tile_hvp<T, 3, true, MB, 0, false>));                             \
+    SET((k_tile_hvp<T, 2, false, MB, 0, false>));                            \
+    SET((k_tile_hvp<T, 3, false, MB, 0, false>));                            \
+    SET((k_tile_hvp<T, 2, true, MB, 0, true>));                              \
+    SET((k_tile_hvp<T, 3, true, MB, 0, true>));                              \
+    SET((k_tile_hvp<T, 2, false, MB, 0, true>));                             \
+    SET((k_tile_hvp<T, 3, false, MB, 0, true>));                             \
+    SET((k_tile_hvp<T, 2, true, MB, (sizeof(T) == 4 ? kCap2 : 0), false>));  \
+    SET((k_tile_hvp<T, 3, true, MB, (sizeof(T) == 4 ? kCap3 : 0), false>));  \
+    SET((k_tile_hvp<T, 2, false, MB, (sizeof(T) == 4 ? kCap2 : 0), false>)); \
+    SET((k_tile_hvp<T, 3, false, MB, (sizeof(T) == 4 ? kCap3 : 0), false>));
     SET_HVP(float, 3)
     SET_HVP(float, 4)
     SET_HVP(double, 1)
