@@ -557,26 +557,42 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         store_corners<T, D>(sE, mte, le, G);  // overwrites this element's own columns only
     }
     __syncthreads();
-    double dot = (double)qsum;
+    // p.Ap of this thread in the kernel's precision: in the mixed kernel the
+    // block sum stays FP32 too (GB300's FP64 pipe runs at 1/64 of FP32) and
+    // the tile partials are summed with compensation by k_cg_alpha.
+    T dot = qsum;
+    const bool contact = ph.kc > 0.0, dyn = ph.dyn != 0;
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int code = sCode[k];
         if (code == LV_PAD) continue;
         T acc[D];
         gather_corners<T, D>(sInc, sLinc[k], sE, mte, acc);
         const int64_t gid = sGid[k];
-        if (code == LV_INTERIOR) {
-            if (ph.kc > 0.0) {
+        const bool interior = code == LV_INTERIOR;
+        const bool owner = CG && (interior || (code & 1));  // counts the vertex terms of p.Ap
+        if ((interior || owner) && (contact || dyn)) {
+            T kcv = T(0), m = T(0), mh = T(0);  // contact curvature and inertia (+ friction) diagonals
+            if (contact) {
                 const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
                 const double pen = yy < 0.0 ? -yy : 0.0;
                 const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-                acc[1] += T(ph.s_el * d2) * sv[k * D + 1];
+                kcv = T(ph.s_el * d2);
             }
-            if (ph.dyn) {
-                const T m = T(vd.mass[gid]);
-                const T mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
+            if (dyn) {
+                m = T(vd.mass[gid]);
+                mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
+            }
+            T dv[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) acc[c] += (c == 1 ? m : mh) * sv[k * D + c];
-            }
+            for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * sv[k * D + c];
+            if (interior)
+#pragma unroll
+                for (int c = 0; c < D; ++c) acc[c] += dv[c];
+            if (owner)
+#pragma unroll
+                for (int c = 0; c < D; ++c) dot += dv[c] * sv[k * D + c];
+        }
+        if (interior) {
             const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
             for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
@@ -584,92 +600,47 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
 #pragma unroll
             for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
         }
-        if (CG && (code == LV_INTERIOR || (code & 1)) && (ph.kc > 0.0 || ph.dyn)) {
-            // per-vertex terms of p.Ap, counted once by the vertex's owner tile
-            double vt = 0.0;
-            if (ph.kc > 0.0) {
-                const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
-                const double pen = yy < 0.0 ? -yy : 0.0;
-                const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-                vt += ph.s_el * d2 * (double)sv[k * D + 1] * (double)sv[k * D + 1];
-            }
-            if (ph.dyn) {
-                double v2 = 0.0, h2 = 0.0;
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const double q = (double)sv[k * D + c] * (double)sv[k * D + c];
-                    v2 += q;
-                    if (c != 1) h2 += q;
-                }
-                vt += vd.mass[gid] * v2;
-                if (ph.fw) vt += ph.fw[gid] * h2;
-            }
-            dot += vt;
-        }
     }
     pdl_trigger();  // the alpha reduction may be scheduled once every tile is done
     if (CG) {
-        const double s = block_sum(dot);
-        if (threadIdx.x == 0) partials[t] = s;  // reduced by k_cg_alpha
+        const T sum = block_sum(dot);
+        if (threadIdx.x == 0) reinterpret_cast<T *>(partials)[t] = sum;  // reduced by k_cg_alpha<T>
     }
 }
 
-template <typename T, int D, bool CG>
+// Completes y = A v at halo vertices: the tiles' partial sums in tile order
+// plus the per-vertex terms.
+template <typename T, int D>
 __global__ void __launch_bounds__(256) k_fin_hvp(TileDev td, VertDev vd, Phys ph, const T *__restrict__ u,
-                                                 const T *__restrict__ v, const T *__restrict__ hp, T *__restrict__ y,
-                                                 double *__restrict__ partials, DevScalars *__restrict__ sc)
+                                                 const T *__restrict__ v, const T *__restrict__ hp, T *__restrict__ y)
 {
-    if (CG && sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double dot = 0.0;
-    if (i < td.n_fin) {
-        const int64_t gid = td.fin_gid[i];
-        const bool fx = vd.fixed[gid] != 0;
-        T acc[D];
+    if (i >= td.n_fin) return;
+    const int64_t gid = td.fin_gid[i];
+    const bool fx = vd.fixed[gid] != 0;
+    T acc[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = T(0);
-        for (int s = td.fin_ptr[i]; s < td.fin_ptr[i + 1]; ++s)
+    for (int c = 0; c < D; ++c) acc[c] = T(0);
+    for (int s = td.fin_ptr[i]; s < td.fin_ptr[i + 1]; ++s)
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] += hp[(int64_t)s * D + c];
-        T vv[D];
+        for (int c = 0; c < D; ++c) acc[c] += hp[(int64_t)s * D + c];
+    T vv[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) vv[c] = fx ? T(0) : v[gid * D + c];
-        if (ph.kc > 0.0) {
-            const double yy = vd.X[gid * D + 1] + (double)u[gid * D + 1];
-            const double pen = yy < 0.0 ? -yy : 0.0;
-            const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-            acc[1] += T(ph.s_el * d2) * vv[1];
-        }
-        if (ph.dyn) {
-            const T m = T(vd.mass[gid]);
-            const T mh = ph.fw ? m + T(ph.fw[gid]) : m;
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] += (c == 1 ? m : mh) * vv[c];
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const T o = fx ? T(0) : acc[c];
-            y[gid * D + c] = o;
-            if (CG) dot += (double)vv[c] * (double)o;
-        }
+    for (int c = 0; c < D; ++c) vv[c] = fx ? T(0) : v[gid * D + c];
+    if (ph.kc > 0.0) {
+        const double yy = vd.X[gid * D + 1] + (double)u[gid * D + 1];
+        const double pen = yy < 0.0 ? -yy : 0.0;
+        const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+        acc[1] += T(ph.s_el * d2) * vv[1];
     }
-    if (CG) {
-        const double s = block_sum(dot);
-        const int base = td.n_tiles;
-        if (threadIdx.x == 0) partials[base + blockIdx.x] = s;
-        if (last_block(&sc->ticket[TK_FIN], gridDim.x)) {
-            const double pAp = sum_partials(partials, base + gridDim.x);
-            if (threadIdx.x == 0) {
-                sc->pAp = pAp;
-                if (pAp > 0.0 && isfinite(pAp)) {
-                    sc->alpha = sc->rr / pAp;
-                } else {
-                    sc->alpha = 0.0;
-                    sc->negcurv = 1;
-                }
-            }
-        }
+    if (ph.dyn) {
+        const T m = T(vd.mass[gid]);
+        const T mh = ph.fw ? m + T(ph.fw[gid]) : m;
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] += (c == 1 ? m : mh) * vv[c];
     }
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
 }
 
 // ---------------------------------------------------------------- parameter VJP
@@ -913,34 +884,28 @@ static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *a, const
     }
 }
 
-template <typename T, bool CG>
+template <typename T>
 static void hvp_fin(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, const T *hp, cudaStream_t s)
 {
     c.n_launch += 1;
     if (c.dim == 2)
-        k_fin_hvp<T, 2, CG><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y, c.partials, c.sc);
+        k_fin_hvp<T, 2><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y);
     else
-        k_fin_hvp<T, 3, CG><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y, c.partials, c.sc);
+        k_fin_hvp<T, 3><<<c.n_fin_blocks, 256, 0, s>>>(c.td, c.vd, ph, u, v, hp, y);
 }
 
 template <typename T>
-void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, bool with_dot,
-                cudaStream_t s)
+void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
-    if (with_dot) {
-        hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
-        hvp_fin<T, true>(c, ph, u, v, y, hp, s);
-    } else {
-        hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
-        hvp_fin<T, false>(c, ph, u, v, y, hp, s);
-    }
+    hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
+    hvp_fin<T>(c, ph, u, v, y, hp, s);
 }
 
 template <typename T>
 void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
     hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
-    launch_cg_alpha(c, c.td.n_tiles, s);
+    launch_cg_alpha<T>(c, c.td.n_tiles, s);
 }
 
 template <typename T>
@@ -954,7 +919,7 @@ template <typename T>
 void launch_hvp_finalize_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, const T *hp,
                               cudaStream_t s)
 {
-    hvp_fin<T, false>(c, ph, u, v, y, hp, s);
+    hvp_fin<T>(c, ph, u, v, y, hp, s);
 }
 
 void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
@@ -1018,9 +983,9 @@ cudaError_t configure_elem_kernels()
 }
 
 template void launch_hvp<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
-                                float *, bool, cudaStream_t);
+                                float *, cudaStream_t);
 template void launch_hvp<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
-                                 double *, double *, bool, cudaStream_t);
+                                 double *, double *, cudaStream_t);
 template void launch_hvp_cg<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
                                    float *, cudaStream_t);
 template void launch_hvp_cg<double>(const Ctx &, const Phys &, const double *, const double *, const double *,

@@ -142,12 +142,10 @@ void launch_energy(const Ctx &c, const Phys &ph, const double *u, const double *
 void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uhat,
                  const double *a, double *g, double *hp, cudaStream_t s);
 
-// HVP y = A v (A = H, or M + dt^2 H when ph.dyn), masked.  With with_dot,
-// the finalize kernel also forms p.Ap into sc->pAp and the CG step length
-// sc->alpha.  `done` (device int, may be null) skips the launch body when set.
+// HVP y = A v (A = H, or M + dt^2 H when ph.dyn), masked.
 template <typename T>
 void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
-                bool with_dot, cudaStream_t s);
+                cudaStream_t s);
 template <typename T>
 void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y,
                           T *hp, cudaStream_t s);
@@ -212,7 +210,9 @@ void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, d
                      cudaStream_t s);
 // v1 = (x1 - x0)/dt
 int vec_grid_size(int64_t n);
-// one block: alpha from the n_partials p.Ap partials of the HVP tile kernel
+// One block: p.Ap from the HVP tile partials (type T: FP32 partials are summed
+// with compensation) -> sc->alpha, or non-positive curvature.
+template <typename T>
 void launch_cg_alpha(const Ctx &c, int n_partials, cudaStream_t s);
 // r = b - Ax, |r|^2 -> sc->gn2
 void launch_residual(const Ctx &c, const double *b, const double *Ax, double *r, cudaStream_t s);

@@ -1,9 +1,15 @@
-// Deterministic FP64 block reductions and the last-block-done pattern.
+// Deterministic block reductions and the last-block-done pattern.
 //
 // Every reduction writes one partial per block; the block that finishes
 // last (integer ticket, so the result does not depend on arrival order)
 // sums the partials in index order.  Sums therefore come out bit-identical
 // from run to run.
+//
+// FP32 variants serve the mixed-precision CG loop: GB300 executes FP64 at
+// 1/64 of the FP32 rate, so the FP32 kernels keep their block sums in FP32
+// and the one-block reductions of their partials use compensated FP32
+// summation (TwoSum, Knuth), which carries each rounding error forward and
+// loses nothing to a plain FP64 sum of the same partials in practice.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,6 +28,93 @@ __device__ __forceinline__ double warp_min(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP32 sum over the block; the result is valid in thread 0.
+__device__ __forceinline__ float block_sum(float v)
+{
+    __shared__ float redf[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) redf[w] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? redf[lane] : 0.0f;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// s + e == a + b exactly (six FP32 additions; no multiplication, so no FMA
+// contraction can change it).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) + (h2, l2), renormalised.
+__device__ __forceinline__ void ds_merge(float &hi, float &lo, float h2, float l2)
+{
+    float s, e;
+    two_sum(hi, h2, s, e);
+    e += lo + l2;
+    two_sum(s, e, hi, lo);
+}
+
+// Fixed-order compensated sum of n FP32 partials; valid (as FP64) in thread 0.
+__device__ __forceinline__ double sum_partials(const float *p, int n)
+{
+    float hi[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int bd = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 7 * bd < n; i += 8 * bd) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + i + k * bd);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ds_merge(hi[k], lo[k], v[k], 0.0f);
+    }
+    for (; i < n; i += bd) ds_merge(hi[0], lo[0], __ldcg(p + i), 0.0f);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) ds_merge(hi[0], lo[0], hi[k], lo[k]);
+    float h = hi[0], l = lo[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+        ds_merge(h, l, h2, l2);
+    }
+    __shared__ float rh[32], rl[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        rh[w] = h;
+        rl[w] = l;
+    }
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        h = in ? rh[lane] : 0.0f;
+        l = in ? rl[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+            ds_merge(h, l, h2, l2);
+        }
+        r = (double)h + (double)l;
+    }
+    return r;
 }
 
 // Sum over the block; the result is valid in thread 0.

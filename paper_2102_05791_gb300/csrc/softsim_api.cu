@@ -710,7 +710,7 @@ static int adjoint_impl(sim_handle *h, bool dyn, const double *b, double *lambda
         S.cg_iters_total += it;
         budget -= std::max(it, 1);
         launch_accumulate<T>(c, h->lacc, (const T *)h->vd, s);
-        launch_hvp<double>(c, ph, h->u, h->a64, h->lacc, h->Hx, h->hp64, false, s);
+        launch_hvp<double>(c, ph, h->u, h->a64, h->lacc, h->Hx, h->hp64, s);
         launch_residual(c, h->work, h->Hx, h->r64, s);
         CKL(h);
         if ((rc = read_scalars(h, s))) return rc;
@@ -772,9 +772,9 @@ extern "C" int sim_hvp(sim_handle *h, const double *x, const double *a, const vo
     if ((rc = set_activation(h, a, s))) return rc;
     const Phys ph = make_phys(h, false);
     if (is_mixed(h))
-        launch_hvp<float>(h->ctx, ph, h->u32, h->a32, (const float *)v, (float *)Hv, h->hp32, false, s);
+        launch_hvp<float>(h->ctx, ph, h->u32, h->a32, (const float *)v, (float *)Hv, h->hp32, s);
     else
-        launch_hvp<double>(h->ctx, ph, h->u, h->a64, (const double *)v, (double *)Hv, h->hp64, false, s);
+        launch_hvp<double>(h->ctx, ph, h->u, h->a64, (const double *)v, (double *)Hv, h->hp64, s);
     CKL(h);
     return SIM_OK;
 }

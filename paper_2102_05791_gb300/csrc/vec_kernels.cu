@@ -2,11 +2,13 @@
 //
 // CG (Sec. 3: the adjoint system is solved matrix-free by conjugate
 // gradients; the same CG gives the Newton direction) keeps its scalars in
-// device memory: the finalize kernel of the HVP forms p.Ap and alpha,
-// cg_update forms r.r and beta and raises `done`, so a whole block of
-// iterations runs without a host round trip and can be captured in a CUDA
-// graph.  Every dot product is accumulated in FP64 with fixed-order
-// reductions.  Vectors are float (mixed precision) or double.
+// device memory: the HVP tile kernel and k_cg_alpha form p.Ap and alpha,
+// k_cg_update_halo and k_cg_beta form r.r and beta and raise `done`, so a
+// whole block of iterations runs without a host round trip and can be
+// captured in a CUDA graph.  Reductions are fixed-order; vectors are float
+// (mixed precision) or double.  In the float CG loop the block partials are
+// FP32 and the one-block sums over them are compensated FP32 (GB300's FP64
+// rate is 1/64 of FP32); everything else is summed in FP64.
 #include "internal.h"
 #include "reduce.cuh"
 #include "pdl.cuh"
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
     const bool neg = sc->negcurv != 0;
     const bool first = sc->iter == 0;
     const T alpha = T(sc->alpha);
+    const bool contact = ph.kc > 0.0;
     float rr32 = 0.0f;  // at most a few vertices per thread; summed in FP64 across threads
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vd.nv;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
             for (int s = td.fin_ptr[f]; s < td.fin_ptr[f + 1]; ++s)
 #pragma unroll
                 for (int c = 0; c < D; ++c) a[c] += hp[(int64_t)s * D + c];
-            if (ph.kc > 0.0) {
+            if (contact) {
                 const double yy = vd.X[i * D + 1] + (double)u[i * D + 1];
                 const double pen = yy < 0.0 ? -yy : 0.0;
                 const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
@@ -146,17 +149,24 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
             rr32 += (float)ri * (float)ri;
         }
     }
-    const double s = block_sum((double)rr32);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;  // reduced by k_cg_beta
+    if constexpr (sizeof(T) == 4) {  // FP32 partials, summed with compensation by k_cg_beta<float>
+        const float s = block_sum(rr32);
+        if (threadIdx.x == 0) reinterpret_cast<float *>(partials)[blockIdx.x] = s;
+    } else {
+        const double s = block_sum((double)rr32);
+        if (threadIdx.x == 0) partials[blockIdx.x] = s;  // reduced by k_cg_beta<double>
+    }
 }
 
 // One block: p.Ap from the HVP tile partials -> alpha (or non-positive curvature).
+// PT is the partials' type (float: compensated FP32 sum).
+template <typename PT>
 __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ partials, int n, DevScalars *sc)
 {
     pdl_trigger();
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
-    const double pAp = sum_partials(partials, n);
+    const double pAp = sum_partials(reinterpret_cast<const PT *>(partials), n);
     if (threadIdx.x == 0) {
         sc->pAp = pAp;
         if (pAp > 0.0 && isfinite(pAp)) {
@@ -169,12 +179,13 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ pa
 }
 
 // One block: r.r from the update partials -> beta, iteration count, done.
+template <typename PT>
 __global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ partials, int n, DevScalars *sc)
 {
     pdl_trigger();
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
-    const double tot = sum_partials(partials, n);
+    const double tot = sum_partials(reinterpret_cast<const PT *>(partials), n);
     if (threadIdx.x == 0) {
         if (sc->negcurv) {
             sc->done = 1;
@@ -417,13 +428,14 @@ void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r,
     else
         launch_k(c.pdl, k_cg_update_halo<T, 3>, dim3(g), dim3(256), 0, s, c.td, c.vd, ph, u, d, r, p, Ap, hp,
                  c.partials, c.sc);
-    launch_k(c.pdl, k_cg_beta, dim3(1), dim3(1024), 0, s, (const double *)c.partials, g, c.sc);
+    launch_k(c.pdl, k_cg_beta<T>, dim3(1), dim3(1024), 0, s, (const double *)c.partials, g, c.sc);
 }
 
+template <typename T>
 void launch_cg_alpha(const Ctx &c, int n_partials, cudaStream_t s)
 {
     c.n_launch += 1;
-    launch_k(c.pdl, k_cg_alpha, dim3(1), dim3(1024), 0, s, (const double *)c.partials, n_partials, c.sc);
+    launch_k(c.pdl, k_cg_alpha<T>, dim3(1), dim3(1024), 0, s, (const double *)c.partials, n_partials, c.sc);
 }
 
 template <typename T>
@@ -524,6 +536,7 @@ int vec_grid_size(int64_t n) { return vec_grid(n); }
     template void launch_cg_update_halo<T>(const Ctx &, const Phys &, const T *, T *, T *, const T *, const T *,    \
                                            const T *, cudaStream_t);                                                \
     template void launch_cg_dir<T>(const Ctx &, T *, const T *, cudaStream_t);                                      \
+    template void launch_cg_alpha<T>(const Ctx &, int, cudaStream_t);                                               \
     template void launch_dir_check<T>(const Ctx &, const double *, T *, cudaStream_t);                              \
     template void launch_step_update<T>(const Ctx &, double *, const T *, double, float *, cudaStream_t);           \
     template void launch_gather_elem<T>(const Ctx &, const double *, T *, cudaStream_t);                            \
