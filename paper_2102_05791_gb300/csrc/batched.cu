@@ -49,6 +49,7 @@ struct BatchDev {
     const double *mu = nullptr, *lam = nullptr;      // [M]
     double k = 0, grav = 0, kc = 0, dt = 0;
     double kf = 0, feps = 0;  // ground friction k_f and its height; kf == 0: off
+    float k_f = 0, dt2_f = 0;  // FP32 copies of k and dt^2
     int cpow = 3, log_mode = 0, muscle = 0;
     double newton_rtol = 1e-8, adj_rtol = 1e-6;
     int max_newton = 100, max_cg = 500, max_adj_cg = 2000, max_ls = 30;
@@ -57,6 +58,10 @@ struct BatchDev {
            *lacc = nullptr, *xbar = nullptr, *vbar = nullptr;
     double *fw = nullptr, *u0 = nullptr;  // friction: [V] 2 k_f ReLU(eps - y0), [V][d] x0 - X (kf > 0 only)
     float *u32 = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
+    // FP32 HVP inputs fixed during one CG solve (no FP64 arithmetic or
+    // conversion inside the CG loop; GB300's FP64 rate is 1/64 of FP32):
+    float *a32 = nullptr;   // [E] the step's activations
+    float *dg32 = nullptr;  // [V][2] vertex diagonal: horizontal (m + fw), vertical (m + h^2 contact'')
     float *c32 = nullptr;   // corners [E*(d+1)][d]
     double *c64 = nullptr;
     int *counter = nullptr;
@@ -68,6 +73,7 @@ struct Mesh {
     int64_t v0, e0;
     int nv, ne;
     double mu, lam;
+    float mu_f, lam_f;
 };
 
 // Block-wide sum broadcast to every thread (fixed order).
@@ -82,6 +88,36 @@ __device__ double bsum(double v, double *red)
         double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
         t = warp_sum(t);
         if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Block-wide compensated sum of FP32 values (TwoSum pairs), as FP64,
+// broadcast to every thread (fixed order).
+__device__ double bsum_f(float v, double *red)
+{
+    float h = v, l = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+        ds_merge(h, l, h2, l2);
+    }
+    float2 *rf = reinterpret_cast<float2 *>(red);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) rf[w] = make_float2(h, l);
+    __syncthreads();
+    if (w == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        h = in ? rf[lane].x : 0.0f;
+        l = in ? rf[lane].y : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+            ds_merge(h, l, h2, l2);
+        }
+        if (lane == 0) red[32] = (double)h + (double)l;
     }
     __syncthreads();
     return red[32];
@@ -321,12 +357,15 @@ template <typename T, int D>
 __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, const T *us, const T *v, T *y, T *c,
                            const T *ed, double *red)
 {
-    const T s_el = T(b.dt * b.dt);
-    const T mu = T(m.mu), lam = T(m.lam);
+    constexpr bool F32 = sizeof(T) == 4;
+    const T s_el = pick<T>(b.dt * b.dt, b.dt2_f);
+    const T mu = pick<T>(m.mu, m.mu_f), lam = pick<T>(m.lam, m.lam_f);
+    const T kk = pick<T>(b.k, b.k_f);
     for (int le = threadIdx.x; le < m.ne; le += blockDim.x) {
         const int64_t e = m.e0 + le;
         int lid[D + 1];
         elem_ids<D>(b, e, lid);
+        const T ae = F32 ? T(b.a32[e]) : T(a_t[e]);
         T B[D][D], gv[D], W, f[D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D];
         load_elem<T, D>(ed, b.estride, e, B, gv, W, f);
         edge_of<T, T, D>(us, m, lid, Du);
@@ -354,7 +393,7 @@ __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, 
             for (int j = 0; j < D; ++j) dJ += C[i][j] * dF[i][j];
         T l, cc, cp;
         log_terms<T>(b.log_mode, mu, lam, J, l, cc, cp);
-        const T ka = T(b.k * a_t[e]);
+        const T ka = F32 ? kk * ae : T(b.k * a_t[e]);
         T dvg[D];  // (d2psi_m/dq2) dq with dq = Dv g
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -375,7 +414,7 @@ __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, 
                 qdq += s * dvg[i];
             }
             T c1, c2;
-            spring_terms<T>(W != T(0), T(b.k), T(a_t[e]), sqrt(s2), c1, c2);
+            spring_terms<T>(W != T(0), kk, ae, sqrt(s2), c1, c2);
 #pragma unroll
             for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
         } else {
@@ -395,27 +434,36 @@ __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, 
         put_corners<T, D>(c, e, G);
     }
     __syncthreads();
-    double dot = 0.0;
+    T dot = T(0);
     for (int lv = threadIdx.x; lv < m.nv; lv += blockDim.x) {
         const int64_t vg = m.v0 + lv;
         T acc[D];
         corner_sum<T, D>(b, m, c, lv, acc);
         const bool fx = b.fixed[vg] != 0;
-        const T mass = T(b.mass[vg]);
-        const double yy = b.X[vg * D + 1] + (double)us[vg * D + 1];
+        T dh, dy;  // diagonal: horizontal axes (inertia + friction), y (inertia + contact)
+        if constexpr (F32) {
+            dh = b.dg32[2 * vg];
+            dy = b.dg32[2 * vg + 1];
+        } else {
+            const double mass = b.mass[vg];
+            const double yy = b.X[vg * D + 1] + us[vg * D + 1];
+            dh = b.fw ? mass + b.fw[vg] : mass;  // friction stiffens the horizontal axes
+            dy = mass + b.dt * b.dt * contact_d2(yy, b.kc, b.cpow);
+        }
         T vv[D];
 #pragma unroll
         for (int q = 0; q < D; ++q) vv[q] = fx ? T(0) : v[vg * D + q];
-        acc[1] += T(b.dt * b.dt * contact_d2(yy, b.kc, b.cpow)) * vv[1];
-        const T mh = b.fw ? mass + T(b.fw[vg]) : mass;  // friction stiffens the horizontal axes
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-            const T o = fx ? T(0) : acc[q] + (q == 1 ? mass : mh) * vv[q];
+            const T o = fx ? T(0) : acc[q] + (q == 1 ? dy : dh) * vv[q];
             y[vg * D + q] = o;
-            dot += (double)vv[q] * (double)o;
+            dot += vv[q] * o;
         }
     }
-    return bsum(dot, red);
+    if constexpr (F32)
+        return bsum_f(dot, red);
+    else
+        return bsum(dot, red);
 }
 
 // CG on (M + h^2 H) d = rhs (FP64 rhs, FP32 vectors); returns iterations.
@@ -424,15 +472,15 @@ __device__ int cg_solve(const BatchDev &b, const Mesh &m, const double *a_t, con
                         double *red)
 {
     const int64_t o = m.v0 * D, n = (int64_t)m.nv * D;
-    double rr = 0.0;
+    float rr32 = 0.0f;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const float ri = (float)rhs[o + i];
         b.r[o + i] = ri;
         b.p[o + i] = ri;
         b.d[o + i] = 0.0f;
-        rr += (double)ri * (double)ri;
+        rr32 += ri * ri;
     }
-    rr = bsum(rr, red);
+    double rr = bsum_f(rr32, red);
     const double tol2 = rtol * rtol * rr;
     int k = 0;
     for (; k < max_it; ++k) {
@@ -445,14 +493,14 @@ __device__ int cg_solve(const BatchDev &b, const Mesh &m, const double *a_t, con
             break;
         }
         const float alpha = (float)(rr / pAp);
-        double rn = 0.0;
+        float rn32 = 0.0f;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
             b.d[o + i] += alpha * b.p[o + i];
             const float ri = b.r[o + i] - alpha * b.Ap[o + i];
             b.r[o + i] = ri;
-            rn += (double)ri * (double)ri;
+            rn32 += ri * ri;
         }
-        rn = bsum(rn, red);
+        const double rn = bsum_f(rn32, red);
         const float beta = (float)(rn / rr);
         rr = rn;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.p[o + i] = b.r[o + i] + beta * b.p[o + i];
@@ -461,9 +509,26 @@ __device__ int cg_solve(const BatchDev &b, const Mesh &m, const double *a_t, con
     return k;
 }
 
-__device__ __forceinline__ void set_u32(const BatchDev &b, int64_t o, int64_t n)
+// FP32 state and vertex diagonals of mesh m for the CG solves at the current
+// u (the caller synchronises before the next pass reads them).
+template <int D>
+__device__ void set_fp32_state(const BatchDev &b, const Mesh &m)
 {
+    const int64_t o = m.v0 * D, n = (int64_t)m.nv * D;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.u32[o + i] = (float)b.u[o + i];
+    for (int lv = threadIdx.x; lv < m.nv; lv += blockDim.x) {
+        const int64_t v = m.v0 + lv;
+        const double mass = b.mass[v];
+        const double yy = b.X[v * D + 1] + b.u[v * D + 1];
+        b.dg32[2 * v] = (float)(b.fw ? mass + b.fw[v] : mass);
+        b.dg32[2 * v + 1] = (float)(mass + b.dt * b.dt * contact_d2(yy, b.kc, b.cpow));
+    }
+}
+
+// FP32 activations of mesh m for this step.
+__device__ void set_a32(const BatchDev &b, const Mesh &m, const double *a_t)
+{
+    for (int le = threadIdx.x; le < m.ne; le += blockDim.x) b.a32[m.e0 + le] = (float)a_t[m.e0 + le];
 }
 
 // Friction data of a step of mesh m started at x0: u0 = x0 - X and
@@ -492,6 +557,7 @@ __device__ int step_forward(const BatchDev &b, const Mesh &m, const double *x0, 
         b.uhat[o + i] = x0[o + i] + b.dt * v0[o + i] - b.X[o + i];
     }
     if (b.fw) friction_prep<D>(b, m, x0);
+    set_a32(b, m, a_t);
     __syncthreads();
     double S0;
     double gn = sqrt(grad_pass<D>(b, m, a_t, red));
@@ -509,7 +575,7 @@ __device__ int step_forward(const BatchDev &b, const Mesh &m, const double *x0, 
             break;
         }
         ++*newton_it;
-        set_u32(b, o, n);
+        set_fp32_state<D>(b, m);
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.w64[o + i] = -b.g[o + i];
         __syncthreads();
         const double eta = fmin(0.5, sqrt(gn / g0));
@@ -563,9 +629,9 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
     const double h = b.dt;
     if (b.fw) friction_prep<D>(b, m, x0);
     double bn = 0.0;
+    set_a32(b, m, a_t);
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         b.u[o + i] = x1[o + i] - b.X[o + i];
-        b.u32[o + i] = (float)b.u[o + i];
         const double bi = b.fixed[m.v0 + i / D] ? 0.0 : b.xbar[o + i] + b.vbar[o + i] / h;
         b.w64[o + i] = bi;
         b.r64[o + i] = bi;
@@ -573,6 +639,8 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
         bn += bi * bi;
     }
     bn = sqrt(bsum(bn, red));
+    set_fp32_state<D>(b, m);
+    __syncthreads();
     double rn = bn;
     int status = SIM_ENOTCONVERGED;
     int budget = b.max_adj_cg;
@@ -715,6 +783,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
         m.ne = (int)(b.eoff[mi + 1] - m.e0);
         m.mu = b.mu[mi];
         m.lam = b.lam[mi];
+        m.mu_f = (float)m.mu;
+        m.lam_f = (float)m.lam;
         int status = SIM_OK, newton_it = 0, cg_f = 0, cg_a = 0;
         const size_t VD = (size_t)V * D;
         for (int t = 0; t < n_steps; ++t) {
@@ -951,6 +1021,8 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.kc = m0.k_contact;
     b.dt = m0.dt;
     b.kf = m0.k_friction;
+    b.k_f = (float)m0.k_muscle;
+    b.dt2_f = (float)(m0.dt * m0.dt);
     b.feps = m0.eps_friction;
     b.cpow = m0.contact_power;
     b.log_mode = m0.log_mode;
@@ -976,6 +1048,8 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
         b.u0 = balloc<double>(bt, VD);
     }
     b.u32 = balloc<float>(bt, VD);
+    b.a32 = balloc<float>(bt, (size_t)E);
+    b.dg32 = balloc<float>(bt, (size_t)2 * V);
     b.d = balloc<float>(bt, VD);
     b.r = balloc<float>(bt, VD);
     b.p = balloc<float>(bt, VD);
@@ -987,7 +1061,7 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
     b.mgrad = balloc<double>(bt, (size_t)3 * M);
     const void *ptrs[] = {b.voff, b.eoff, b.order, b.X, b.mass, b.fixed, b.conn, b.vinc_ptr, b.vinc, b.e32, b.e64,
                           b.mu, b.lam, b.u, b.uhat, b.g, b.w64, b.r64, b.Hx, b.lacc, b.xbar, b.vbar, b.u32,
-                          b.d, b.r, b.p, b.Ap, b.c32, b.c64, b.counter, b.mstat, b.mgrad};
+                          b.d, b.r, b.p, b.Ap, b.c32, b.c64, b.counter, b.mstat, b.mgrad, b.a32, b.dg32};
     for (const void *p : ptrs)
         if (!p) return bfail(bt, SIM_ENOMEM, "device allocation or upload failed");
     if (b.kf > 0.0 && (!b.fw || !b.u0)) return bfail(bt, SIM_ENOMEM, "device allocation failed");

@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         }
         return;
     }
-    const T mu = T(ph.mu), lam = T(ph.lam);
-    const T sel = T(ph.s_el), kk = T(ph.k);
+    const T mu = pick<T>(ph.mu, ph.mu_f), lam = pick<T>(ph.lam, ph.lam_f);
+    const T sel = pick<T>(ph.s_el, ph.s_el_f), kk = pick<T>(ph.k, ph.k_f);
     T qsum = T(0);  // CG: sum of the element quadratic forms v_e . (H_e v_e) of this thread
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
         int lid[D + 1];
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     // block sum stays FP32 too (GB300's FP64 pipe runs at 1/64 of FP32) and
     // the tile partials are summed with compensation by k_cg_alpha.
     T dot = qsum;
-    const bool contact = ph.kc > 0.0, dyn = ph.dyn != 0;
+    const bool contact = ph.contact != 0, dyn = ph.dyn != 0;
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int code = sCode[k];
         if (code == LV_PAD) continue;

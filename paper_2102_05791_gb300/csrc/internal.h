@@ -81,14 +81,31 @@ struct Phys {
     int dyn = 0;
     double s_el = 1.0;
     int muscle = 0;              // 0: contractile (k/2) a |F f|^2; 1: active spring (k/2)(|F f|/a - 1)^2
+    // FP32 copies for the FP32 kernels (GB300 converts FP64 at the FP64 rate, 1/64 of FP32)
+    float mu_f = 0, lam_f = 0, k_f = 0, s_el_f = 1;
+    int contact = 0;             // kc > 0
     const double *fw = nullptr;  // [nv] 2 k_f ReLU(eps - y0), or null: no friction
     const double *u0 = nullptr;  // [nv][dim] displacement x0 - X of the step's start
 };
+
+#ifdef __CUDACC__
+// A constant in the kernel's precision, from its FP64 value or its FP32 copy
+// rounded once elsewhere (no conversion in every thread).
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f)
+{
+    if constexpr (sizeof(T) == 4)
+        return f;
+    else
+        return d;
+}
+#endif
 
 // Scalars that the kernels exchange in device memory (no host round trip).
 struct DevScalars {
     // conjugate gradients
     double rr, tol2, pAp, alpha, beta;
+    float alpha_f, beta_f;  // FP32 copies of alpha and beta for the FP32 vector kernels
     int iter, max_iter, done, negcurv;
     // Newton
     double gn2;      // |g|^2 of the FP64 gradient

@@ -118,6 +118,11 @@ static Phys make_phys(const sim_handle *h, bool dyn)
     ph.muscle = h->mat.muscle_model;
     ph.dyn = dyn ? 1 : 0;
     ph.s_el = dyn ? h->mat.dt * h->mat.dt : 1.0;
+    ph.mu_f = (float)ph.mu;
+    ph.lam_f = (float)ph.lam;
+    ph.k_f = (float)ph.k;
+    ph.s_el_f = (float)ph.s_el;
+    ph.contact = ph.kc > 0.0 ? 1 : 0;
     if (dyn && h->fw) {
         ph.fw = h->fw;
         ph.u0 = h->u0;

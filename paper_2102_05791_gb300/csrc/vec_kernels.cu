@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__rest
             sc->max_iter = max_iter;
             sc->negcurv = 0;
             sc->alpha = sc->beta = sc->pAp = 0.0;
+            sc->alpha_f = sc->beta_f = 0.0f;
             sc->done = (tot <= sc->tol2 || max_iter <= 0 || !isfinite(tot)) ? 1 : 0;
         }
     }
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, T *__restrict__ d,
     if (sc->done) return;
     const bool neg = sc->negcurv != 0;
     const bool first = sc->iter == 0;
-    const T alpha = T(sc->alpha);
+    const T alpha = pick<T>(sc->alpha, sc->alpha_f);
     double rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (neg) {
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, T *__restrict__ d,
                 sc->done = 1;
             } else {
                 sc->beta = tot / sc->rr;
+                sc->beta_f = (float)sc->beta;
                 sc->rr = tot;
                 sc->iter += 1;
                 if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
     if (sc->done) return;
     const bool neg = sc->negcurv != 0;
     const bool first = sc->iter == 0;
-    const T alpha = T(sc->alpha);
+    const T alpha = pick<T>(sc->alpha, sc->alpha_f);
     const bool contact = ph.kc > 0.0;
     float rr32 = 0.0f;  // at most a few vertices per thread; summed in FP64 across threads
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vd.nv;
@@ -171,8 +173,10 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ pa
         sc->pAp = pAp;
         if (pAp > 0.0 && isfinite(pAp)) {
             sc->alpha = sc->rr / pAp;
+            sc->alpha_f = (float)sc->alpha;
         } else {
             sc->alpha = 0.0;
+            sc->alpha_f = 0.0f;
             sc->negcurv = 1;
         }
     }
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ par
             sc->done = 1;
         } else {
             sc->beta = tot / sc->rr;
+            sc->beta_f = (float)sc->beta;
             sc->rr = tot;
             sc->iter += 1;
             if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, co
     pdl_trigger();
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
-    const T beta = T(sc->beta);
+    const T beta = pick<T>(sc->beta, sc->beta_f);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = r[i] + beta * p[i];
 }

@@ -286,3 +286,22 @@ def test_iteration_cap_reports_not_converged():
     sim = make_sim(p, "fp64", max_newton=1)
     x, st = sim.solve(dev(p.a), check=False)
     assert st["status"] == -4 and st["newton_iters"] == 1
+
+
+def test_mixed_cg_iterations_track_fp64():
+    """The FP32 CG loop (FP32 step lengths and compensated FP32 sums) takes
+    about as many iterations as the FP64 one on the same solves; a broken
+    step length or direction update shows up here as a large excess."""
+    p = synth.make_small3d(8, 4, 4, split=5, seed=31)
+    its = {}
+    for precision in ("fp64", "mixed"):
+        sim = make_sim(p, precision, tile_elems=128, adjoint_rtol=1e-6)
+        a = dev(p.a)
+        x, st = sim.solve(a)
+        assert st["status"] == 0, st
+        gL = oracle.mean_loss_grad(host(x), p.target)
+        _, sta = sim.adjoint(x, a, dev(gL))
+        its[precision] = (st["cg_iters_total"], sta["cg_iters_total"])
+        sim.close()
+    for k in range(2):
+        assert its["mixed"][k] <= 1.25 * its["fp64"][k] + 10, its
