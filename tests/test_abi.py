@@ -72,3 +72,64 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def _valid_inputs():
+    import numpy as np
+
+    from paper_2102_05791_gb300 import _lib
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    T = np.array([[0, 1, 2]], dtype=np.int32)
+    fib = np.array([[1.0, 0.0]])
+    keep = (X, T, fib)
+    mesh = _lib.SimMesh(2, 3, 1, X.ctypes.data, T.ctypes.data, None)
+    mat = _lib.SimMaterial(1e4, 4e4, 5e3, 1e3, 9.8, 0.0, 3, 0, 0.0, fib.ctypes.data, 0.0, 0.01, 0)
+    return keep, mesh, mat
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("dim", b"dim must be 2 or 3"),
+    ("empty", b"empty mesh"),
+    ("huge", b"too large"),
+    ("cpow", b"contact_power"),
+    ("log", b"log_mode"),
+    ("muscle", b"muscle_model"),
+    ("dt", b"bad material scalar"),
+    ("nan_mu", b"bad material scalar"),
+    ("friction", b"k_friction"),
+    ("precision", b"precision"),
+])
+def test_create_rejects_invalid_inputs_before_touching_the_gpu(lib_path, case, msg):
+    """sim_create validates its host arguments first: each bad input returns
+    SIM_EINVAL with a message (no GPU call is made, so this runs on the CPU)."""
+    from paper_2102_05791_gb300 import _lib
+    L = _lib.load(lib_path)
+    keep, mesh, mat = _valid_inputs()
+    opt = _lib.SimOptions()
+    L.sim_default_options(ctypes.byref(opt))
+    if case == "dim":
+        mesh.dim = 4
+    elif case == "empty":
+        mesh.n_elem = 0
+    elif case == "huge":
+        mesh.n_vert = (1 << 30) + 1
+    elif case == "cpow":
+        mat.contact_power = 4
+    elif case == "log":
+        mat.log_mode = 7
+    elif case == "muscle":
+        mat.muscle_model = 2
+    elif case == "dt":
+        mat.dt = -1.0
+    elif case == "nan_mu":
+        mat.mu = float("nan")
+    elif case == "friction":
+        mat.k_friction = -1.0
+    elif case == "precision":
+        opt.precision = 5
+    h = ctypes.c_void_p()
+    rc = L.sim_create(ctypes.byref(mesh), ctypes.byref(mat), ctypes.byref(opt), ctypes.byref(h))
+    assert rc == _lib.SIM_EINVAL
+    assert not h.value
+    assert msg in L.sim_last_error(None)
+    assert L.sim_create(None, ctypes.byref(mat), ctypes.byref(opt), ctypes.byref(h)) == _lib.SIM_EINVAL
