@@ -91,7 +91,7 @@ def run_batched(dev, steps, warmup, plain_sample=8):
     from paper_2102_05791_gb300 import api
     probs, x0, a_seq, xbT = c4_inputs()
     n_steps = a_seq.shape[0]
-    bt = api.Batch(probs, newton_rtol=1e-8, adjoint_rtol=1e-8, device=dev)
+    bt = api.Batch(probs, newton_rtol=1e-8, adjoint_rtol=1e-8, threads="auto", device=dev)
     X0 = torch.from_numpy(x0).to(dev)
     V0 = torch.zeros_like(X0)
     A = torch.from_numpy(a_seq).to(dev)
@@ -115,6 +115,7 @@ def run_batched(dev, steps, warmup, plain_sample=8):
     res = {"workload": "1,024 2D bodies, tris log-uniform in [200, 8000] (total %d tris), 60 backward-Euler "
                        "steps forward + BPTT" % bt.E,
            "batched_ms_per_rollout": ms, "solves_per_s": solves / (ms / 1e3),
+           "threads_per_mesh": bt.threads, "threads_picked_by": "paper_2102_05791_gb300.autotune",
            "bodies_failed": int((mstat[:, 0] != 0).sum()),
            "newton_iters": int(mstat[:, 1].sum()), "cg_iters_fwd": int(mstat[:, 2].sum()),
            "cg_iters_adj": int(mstat[:, 3].sum())}

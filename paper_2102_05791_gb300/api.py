@@ -265,9 +265,16 @@ class Batch:
     """
 
     def __init__(self, problems, newton_rtol=1e-8, adjoint_rtol=1e-6, max_newton=100, max_cg=500,
-                 max_adjoint_cg=2000, max_ls=30, device=None):
+                 max_adjoint_cg=2000, max_ls=30, threads=0, device=None):
         self._lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if threads == "auto":
+            from . import autotune
+            with torch.cuda.device(self.device):
+                threads = autotune.best_batch_threads(problems, newton_rtol=newton_rtol, adjoint_rtol=adjoint_rtol,
+                                                      max_newton=max_newton, max_cg=max_cg,
+                                                      max_adjoint_cg=max_adjoint_cg, max_ls=max_ls)
+        self.threads = int(threads) if threads else 256
         self._keep = []
         n = len(problems)
         meshes = (L.SimMesh * n)()
@@ -286,6 +293,7 @@ class Batch:
         self._lib.sim_default_options(C.byref(opt))
         opt.newton_rtol, opt.adjoint_rtol = float(newton_rtol), float(adjoint_rtol)
         opt.max_newton, opt.max_cg, opt.max_adjoint_cg, opt.max_ls = int(max_newton), int(max_cg), int(max_adjoint_cg), int(max_ls)
+        opt.threads = self.threads
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             rc = self._lib.sim_batch_create(n, meshes, mats, C.byref(opt), C.byref(h))

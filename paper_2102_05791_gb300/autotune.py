@@ -1,4 +1,5 @@
-"""Autotuner for the tile shape of the HVP kernel.
+"""Autotuners: the tile shape of the HVP kernel, and the block size of the
+batched persistent solver.
 
 For a mesh, tries candidate (elements per tile, threads per block) pairs:
 builds a handle for each, runs a short adjoint CG solve at the rest shape
@@ -99,5 +100,58 @@ def best_tile_shape(X, T, fixed=None, fiber=None, precision: str = "mixed", cand
     best = min(times, key=times.get)
     if use_cache:
         cache[key] = {"best": list(best), "ms": {f"{k[0]}x{k[1]}": v for k, v in times.items()}}
+        _store(cache)
+    return best
+
+
+BATCH_CANDIDATES = (128, 256, 512)
+
+
+def _batch_key(problems) -> str:
+    import torch
+    name = torch.cuda.get_device_name(torch.cuda.current_device())
+    dim = int(problems[0].X.shape[1])
+    n_e = sum(int(p.T.shape[0]) for p in problems)
+    return (f"{name}|batch|d{dim}|m2^{int(math.log2(max(len(problems), 1)))}"
+            f"|e2^{int(math.log2(max(n_e / max(len(problems), 1), 1)))}")
+
+
+def measure_batch(problems, threads: int, n_steps: int = 2, **opt) -> float:
+    """Milliseconds of one batched rollout + BPTT of n_steps steps (after a warm-up run)."""
+    import torch
+
+    from . import api
+    b = api.Batch(problems, threads=threads, **opt)
+    try:
+        dev = b.device
+        x0 = torch.from_numpy(np.concatenate([p.X for p in problems])).to(dev)
+        v0 = torch.zeros_like(x0)
+        rng = np.random.default_rng(0)
+        a = torch.from_numpy(rng.uniform(0.2, 0.9, size=(n_steps, b.E))).to(dev)
+        xb = torch.from_numpy(rng.standard_normal(tuple(x0.shape))).to(dev)
+        b.rollout(x0, v0, a, xb, torch.zeros_like(x0))  # warm-up: graph capture, module loading
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.rollout(x0, v0, a, xb, torch.zeros_like(x0))
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+    finally:
+        b.close()
+
+
+def best_batch_threads(problems, candidates=None, use_cache: bool = True, **opt) -> int:
+    """Threads per mesh CTA with the fastest short batched rollout of these meshes."""
+    key = _batch_key(problems)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return int(cache[key]["best"])
+    times = {}
+    for th in (candidates or BATCH_CANDIDATES):
+        times[th] = measure_batch(problems, th, **opt)
+    best = min(times, key=times.get)
+    if use_cache:
+        cache[key] = {"best": best, "ms": {str(k): v for k, v in times.items()}}
         _store(cache)
     return best

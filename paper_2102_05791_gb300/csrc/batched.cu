@@ -761,8 +761,10 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
     return status;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+// BT threads per mesh CTA (128, 256 or 512; every variant may use up to
+// 128 registers a thread).
+template <int D, int BT>
+__global__ void __launch_bounds__(BT, 512 / BT)
     k_batch_rollout(BatchDev b, int n_steps, const double *__restrict__ a_seq, double *xs, double *vs,
                     const double *__restrict__ xbarT, const double *__restrict__ vbarT, double *__restrict__ abar_seq,
                     int64_t V, int64_t E)
@@ -821,6 +823,16 @@ thread_local std::string g_batch_error;
 
 }  // namespace
 
+using BatchKernel = void (*)(BatchDev, int, const double *, double *, double *, const double *, const double *,
+                             double *, int64_t, int64_t);
+
+static BatchKernel batch_kernel(int dim, int threads)
+{
+    if (dim == 2)
+        return threads == 128 ? k_batch_rollout<2, 128> : threads == 512 ? k_batch_rollout<2, 512> : k_batch_rollout<2, 256>;
+    return threads == 128 ? k_batch_rollout<3, 128> : threads == 512 ? k_batch_rollout<3, 512> : k_batch_rollout<3, 256>;
+}
+
 struct sim_batch {
     int M = 0, dim = 0;
     int64_t V = 0, E = 0;
@@ -830,6 +842,7 @@ struct sim_batch {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = -1;
     const void *graph_args[8] = {};
+    int threads = kBatchThreads;  // threads per mesh CTA
     std::string err;
 };
 
@@ -900,6 +913,9 @@ static int batch_create_impl(sim_batch *bt, int M, const sim_mesh *meshes, const
         o = *opt;
     else
         sim_default_options(&o);
+    if (o.threads != 0 && o.threads != 128 && o.threads != 256 && o.threads != 512)
+        return bfail(bt, SIM_EINVAL, "batched threads per mesh must be 0 (default 256), 128, 256 or 512");
+    bt->threads = o.threads ? o.threads : kBatchThreads;
     bt->voff.assign(M + 1, 0);
     bt->eoff.assign(M + 1, 0);
     for (int m = 0; m < M; ++m) {
@@ -1107,8 +1123,8 @@ extern "C" int sim_batch_rollout(sim_batch *bt, int n_steps, double *states_x, d
     int dev = 0, sms = 0, occ = 0;
     BCK(bt, cudaGetDevice(&dev));
     BCK(bt, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const void *kfun = bt->dim == 2 ? (const void *)k_batch_rollout<2> : (const void *)k_batch_rollout<3>;
-    BCK(bt, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfun, kBatchThreads, 0));
+    const BatchKernel kfun = batch_kernel(bt->dim, bt->threads);
+    BCK(bt, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfun, bt->threads, 0));
     const int grid = std::max(1, std::min(bt->M, sms * std::max(occ, 1)));
     const void *args[8] = {states_x, states_v, a_seq, xbarT, vbarT, abar_seq, (const void *)(intptr_t)n_steps, nullptr};
     const bool reuse = bt->graph && bt->graph_steps == n_steps && memcmp(args, bt->graph_args, sizeof(args)) == 0;
@@ -1123,12 +1139,8 @@ extern "C" int sim_batch_rollout(sim_batch *bt, int n_steps, double *states_x, d
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaMemsetAsync(b.counter, 0, sizeof(int), cap);
-            if (bt->dim == 2)
-                k_batch_rollout<2><<<grid, kBatchThreads, 0, cap>>>(b, n_steps, a_seq, states_x, states_v, xbarT, vbarT,
-                                                                   abar_seq, bt->V, bt->E);
-            else
-                k_batch_rollout<3><<<grid, kBatchThreads, 0, cap>>>(b, n_steps, a_seq, states_x, states_v, xbarT, vbarT,
-                                                                   abar_seq, bt->V, bt->E);
+            kfun<<<grid, bt->threads, 0, cap>>>(b, n_steps, a_seq, states_x, states_v, xbarT, vbarT, abar_seq, bt->V,
+                                                bt->E);
             e = cudaGetLastError();
             cudaError_t e2 = cudaStreamEndCapture(cap, &g);
             if (e == cudaSuccess) e = e2;

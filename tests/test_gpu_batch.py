@@ -69,3 +69,46 @@ def test_batch_rejects_mixed_dims_and_materials():
     probs[1].k_muscle = 1.0
     with pytest.raises(SimError):
         Batch(probs)
+
+
+@pytest.mark.parametrize("threads", [128, 512])
+def test_batch_block_sizes_agree(threads):
+    """Every block size the autotuner may pick gives the 256-thread result
+    within the parity tolerances (the fixed-order sums differ in grouping)."""
+    from paper_2102_05791_gb300.api import Batch
+    probs = _meshes()
+    rng = np.random.default_rng(71)
+    nT = 2
+    x0 = np.concatenate([p.X for p in probs])
+    v0 = 0.1 * rng.standard_normal(x0.shape)
+    xbT = rng.standard_normal(x0.shape)
+    outs = {}
+    for th in (256, threads):
+        b = Batch(probs, adjoint_rtol=1e-8, threads=th)
+        a_seq = rng.uniform(0.0, 1.0, size=(nT, b.E)) if th == 256 else a_seq
+        sx, sv, abar, xb0, vb0, ms = b.rollout(dev(x0), dev(v0), dev(a_seq), dev(xbT), dev(np.zeros_like(x0)))
+        torch.cuda.synchronize()
+        assert (host(ms)[:, 0] == 0).all()
+        outs[th] = (host(sx), host(abar))
+        assert b.threads == th
+        b.close()
+    (s1, g1), (s2, g2) = outs[256], outs[threads]
+    assert np.abs(s1[-1] - s2[-1]).max() <= 1e-6 * np.abs(s1[-1] - s1[0]).max()
+    assert np.linalg.norm(g1 - g2) <= 1e-4 * np.linalg.norm(g1)
+
+
+def test_batch_autotuner_picks_a_candidate(tmp_path, monkeypatch):
+    from paper_2102_05791_gb300 import autotune
+    from paper_2102_05791_gb300.api import Batch
+    monkeypatch.setenv("SOFTSIM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    b = Batch(_meshes(), threads="auto")
+    assert b.threads in autotune.BATCH_CANDIDATES
+    b.close()
+    # second time from the cache
+    assert autotune.best_batch_threads(_meshes()) == b.threads
+
+
+def test_batch_rejects_unsupported_block_size():
+    from paper_2102_05791_gb300.api import Batch, SimError
+    with pytest.raises(SimError):
+        Batch(_meshes(), threads=96)

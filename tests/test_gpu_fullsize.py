@@ -75,7 +75,7 @@ def test_thousand_body_batch_full_size():
     for p in probs:
         xbT[off:off + p.n_vert, 0] = 1.0 / p.n_vert
         off += p.n_vert
-    b = Batch(probs, newton_rtol=1e-8, adjoint_rtol=1e-8)
+    b = Batch(probs, newton_rtol=1e-8, adjoint_rtol=1e-8, threads="auto")
     sx, sv, abar, xb0, vb0, ms = b.rollout(dev(x0), dev(np.zeros_like(x0)), dev(a_seq), dev(xbT),
                                            dev(np.zeros_like(x0)))
     torch.cuda.synchronize()
