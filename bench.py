@@ -162,7 +162,7 @@ def run_dynamics(dev):
     group = torch.from_numpy(p.extra["group"].astype(np.int64)).to(dev)
     sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle, density=p.density,
                         gravity=p.gravity, k_contact=p.k_contact, contact_power=p.contact_power, dt=p.dt,
-                        precision="mixed", device=dev)
+                        precision="mixed", tile_elems="auto", device=dev)
     a_groups = torch.from_numpy(p.extra["a_groups"]).to(dev)
     x0 = torch.from_numpy(p.X).to(dev)
     a_seq = a_groups[:, group].contiguous()
@@ -180,7 +180,7 @@ def run_dynamics(dev):
     dt = time.perf_counter() - t0
     sim.close()
     return {"workload": "64x32 grid (4,096 tris), 200 backward-Euler steps, checkpoints every 20, forward + BPTT "
-                        "(after an untimed 20-step warm-up)",
+                        "(after an untimed 20-step warm-up)", "tile_shape": list(sim.tile_shape),
             "seconds": dt, "steps_per_s": 200 * 2 / dt, "newton_iters": st["newton_iters"] + stb["newton_iters"],
             "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm())}
 
