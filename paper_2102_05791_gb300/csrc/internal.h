@@ -125,7 +125,7 @@ struct TrialT {
     double t[kMaxTrials];
 };
 
-enum Ticket { TK_CG = 0, TK_CGINIT = 1, TK_FIN = 2, TK_ENERGY = 3, TK_GD = 4, TK_GRAD = 5, TK_MISC = 6 };
+enum Ticket { TK_CGINIT = 0, TK_ENERGY = 1, TK_GD = 2, TK_GRAD = 3, TK_MISC = 4 };
 
 // Everything a launcher needs about one mesh.
 struct Ctx {
@@ -185,8 +185,6 @@ void launch_material_vjp(const Ctx &c, const Phys &ph, const double *u, const do
 template <typename T>
 void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p, double rtol,
                     int max_iter, cudaStream_t s);
-template <typename T>
-void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStream_t s);
 // CG update that first completes A p: vertices of one tile take it from Ap
 // (written by the HVP tile kernel), halo vertices add their partial sums hp
 // and their per-vertex terms; then d += alpha p, r -= alpha A p, r.r, beta.

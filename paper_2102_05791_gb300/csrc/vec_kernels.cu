@@ -53,44 +53,6 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__rest
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(int64_t n, T *__restrict__ d, T *__restrict__ r,
-                                                   const T *__restrict__ p, const T *__restrict__ Ap,
-                                                   double *__restrict__ partials, DevScalars *sc)
-{
-    if (sc->done) return;
-    const bool neg = sc->negcurv != 0;
-    const bool first = sc->iter == 0;
-    const T alpha = pick<T>(sc->alpha, sc->alpha_f);
-    double rr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (neg) {
-            if (first) d[i] = p[i];  // no curvature information yet: use the first direction
-        } else {
-            d[i] += alpha * p[i];
-            const T ri = r[i] - alpha * Ap[i];
-            r[i] = ri;
-            rr += (double)ri * (double)ri;
-        }
-    }
-    const double s = block_sum(rr);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-    if (last_block(&sc->ticket[TK_CG], gridDim.x)) {
-        const double tot = sum_partials(partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            if (neg) {
-                sc->done = 1;
-            } else {
-                sc->beta = tot / sc->rr;
-                sc->beta_f = (float)sc->beta;
-                sc->rr = tot;
-                sc->iter += 1;
-                if (tot <= sc->tol2 || sc->iter >= sc->max_iter || !isfinite(tot)) sc->done = 1;
-            }
-        }
-    }
-}
-
 // d += alpha p, r -= alpha A p, r.r -> beta / done, with A p completed here for
 // halo vertices (partial sums in tile order + per-vertex terms).
 template <typename T, int D>
@@ -414,14 +376,6 @@ void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p
 }
 
 template <typename T>
-void launch_cg_update(const Ctx &c, T *d, T *r, const T *p, const T *Ap, cudaStream_t s)
-{
-    c.n_launch += 1;
-    const int64_t n = c.nv * c.dim;
-    k_cg_update<T><<<vec_grid(n), 256, 0, s>>>(n, d, r, p, Ap, c.partials, c.sc);
-}
-
-template <typename T>
 void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
                            const T *hp, cudaStream_t s)
 {
@@ -537,7 +491,6 @@ int vec_grid_size(int64_t n) { return vec_grid(n); }
 
 #define INST(T)                                                                                                     \
     template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, cudaStream_t); \
-    template void launch_cg_update<T>(const Ctx &, T *, T *, const T *, const T *, cudaStream_t);                   \
     template void launch_cg_update_halo<T>(const Ctx &, const Phys &, const T *, T *, T *, const T *, const T *,    \
                                            const T *, cudaStream_t);                                                \
     template void launch_cg_dir<T>(const Ctx &, T *, const T *, cudaStream_t);                                      \
