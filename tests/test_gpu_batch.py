@@ -112,3 +112,59 @@ def test_batch_rejects_unsupported_block_size():
     from paper_2102_05791_gb300.api import Batch, SimError
     with pytest.raises(SimError):
         Batch(_meshes(), threads=96)
+
+
+def _check_batch_against_oracle(probs, a_lo, a_hi, seed, threads=256, tol_g=1e-4):
+    from paper_2102_05791_gb300.api import Batch
+    b = Batch(probs, adjoint_rtol=1e-8, threads=threads)
+    rng = np.random.default_rng(seed)
+    nT = 3
+    a_seq = rng.uniform(a_lo, a_hi, size=(nT, b.E))
+    x0 = np.concatenate([p.X for p in probs])
+    v0 = 0.1 * rng.standard_normal(x0.shape)
+    xbT = rng.standard_normal(x0.shape)
+    vbT = 0.01 * rng.standard_normal(x0.shape)
+    sx, sv, abar, xb0, vb0, ms, mg = b.rollout(dev(x0), dev(v0), dev(a_seq), dev(xbT), dev(vbT),
+                                               material_grad=True)
+    torch.cuda.synchronize()
+    ms = host(ms)
+    assert (ms[:, 0] == 0).all(), ms
+    sx, abar, xb0, vb0, mg = host(sx), host(abar), host(xb0), host(vb0), host(mg)
+    vo, eo = b.vert_offsets, b.elem_offsets
+    for i, p in enumerate(probs):
+        m = oracle.make_model(p)
+        vs_, ve_ = vo[i], vo[i + 1]
+        a_i = a_seq[:, eo[i]:eo[i + 1]]
+        xs, vs = oracle.rollout(m, x0[vs_:ve_], v0[vs_:ve_], a_i, rtol=1e-10)
+        assert np.abs(sx[-1, vs_:ve_] - xs[-1]).max() <= 1e-6 * np.abs(xs[-1] - xs[0]).max()
+        xb, vb, ab, mat = oracle.rollout_backward(m, xs, vs, a_i, xbT[vs_:ve_], vbT[vs_:ve_], material=True)
+        assert np.linalg.norm(abar[:, eo[i]:eo[i + 1]] - ab) <= tol_g * np.linalg.norm(ab)
+        assert np.linalg.norm(vb0[vs_:ve_] - vb) <= tol_g * np.linalg.norm(vb)
+        assert np.linalg.norm(xb0[vs_:ve_] - xb) <= tol_g * np.linalg.norm(xb)
+        assert np.abs(mg[i] - mat).max() <= tol_g * np.abs(mat).max()
+    b.close()
+
+
+@pytest.mark.parametrize("threads", [128, 512])
+def test_batch_3d_tet_meshes(threads):
+    """The 3D persistent kernel: uneven tet meshes with their own mu, forward
+    + BPTT + material gradients against the oracle."""
+    probs = []
+    for i, (nx, ny, nz, split, mu) in enumerate([(2, 2, 2, 5, 1e4), (3, 2, 2, 6, 7e3), (2, 3, 2, 5, 1.5e4)]):
+        p = synth.make_small3d(nx, ny, nz, split=split, fix_bottom=False, seed=100 + i)
+        p.k_contact, p.contact_power, p.dt = 1e6, 3, 1.0 / 30.0
+        p.mu, p.lam = mu, 4.0 * mu
+        probs.append(p)
+    _check_batch_against_oracle(probs, 0.0, 1.0, 101, threads=threads)
+
+
+def test_batch_friction_with_spring_muscle():
+    """Friction and the active-spring muscle together in the batched solver."""
+    probs = []
+    for i, (nx, ny) in enumerate([(4, 2), (6, 3)]):
+        p = synth.make_small2d(nx, ny, fix_bottom=False, seed=110 + i)
+        p.k_contact, p.contact_power, p.dt = 1e5, 2, 1.0 / 30.0
+        p.k_friction, p.eps_friction = 2e3, 0.01
+        p.muscle_model = 1
+        probs.append(p)
+    _check_batch_against_oracle(probs, 0.5, 1.0, 111)
