@@ -199,8 +199,11 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the element-kernel source without its // comment lines: counters
+    taken on the same code stay valid across comment edits."""
     src = os.path.join(ROOT, "paper_2102_05791_gb300", "csrc", "elem_kernels.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    lines = [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
 def recorded_traffic(workload_name):

@@ -352,7 +352,8 @@ __device__ double energy_pass(const BatchDev &b, const Mesh &m, const double *a_
     return Et;
 }
 
-// y = (M + h^2 H(u)) v with pinned rows/columns dropped; returns v.y (FP64 sum).
+// y = (M + h^2 H(u)) v with pinned rows/columns dropped; returns v.y (FP64
+// sum for T = double, compensated FP32 block sum for T = float).
 template <typename T, int D>
 __device__ double hvp_pass(const BatchDev &b, const Mesh &m, const double *a_t, const T *us, const T *v, T *y, T *c,
                            const T *ed, double *red)

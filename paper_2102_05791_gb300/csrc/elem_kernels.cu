@@ -7,7 +7,8 @@
 //   which keeps F accurate in FP32), J = det F,
 //   Psi = mu/2 (|F|^2 - D) - mu l(J) + lambda/2 l(J)^2,
 //   l = log (exact) or q(J) = (J-1) - (J-1)^2/2 (quadratic stand-in),
-//   muscle Psi_m = k/2 a |F f|^2.
+//   muscle Psi_m = k/2 a |F f|^2 (contractile) or k/2 (|F f|/a - 1)^2 (active
+//   spring, Eq. active-spring-potential).
 // Writing P_el = mu F + c(J) cof(F) with c = (lambda l - mu) l', the
 // differential is dP = mu dF + c'(J) (cof F : dF) cof F + c(J) dcof(F)[dF].
 // The element force matrix is G = W dPsi/dF Dm^-T; column j goes to vertex

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
     const bool first = sc->iter == 0;
     const T alpha = pick<T>(sc->alpha, sc->alpha_f);
     const bool contact = ph.kc > 0.0;
-    float rr32 = 0.0f;  // at most a few vertices per thread; summed in FP64 across threads
+    float rr32 = 0.0f;  // at most a few vertices per thread; block-summed (FP32 loop: compensated across blocks)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vd.nv;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (neg) {
