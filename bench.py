@@ -42,6 +42,11 @@ import numpy as np  # noqa: E402
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_TET = 72.0     # conn 16 + Dm^-1 36 + W 4 + fiber 12 + a 4 (FP32 3D HVP)
 BYTES_PER_VERT = 36.0    # read x 12 + read v 12 + write Hv 12
+# FP64 HVP arithmetic per tet (3D), counted from the formulas with an FMA as 2 flops:
+# edges 18, F 54, dF 45, cof 27, dcof 63, J and dJ 22, log terms ~10, muscle 19,
+# stress M 45, G = M B^T + dvg g^T scaled by W 81, p.Ap 18, corner sums 21
+FLOPS_PER_TET_FP64 = 420.0
+FP64_LANES_PER_SM = 2      # 128 FP32 FMA lanes per SM at 1/64 rate on GB300
 
 
 def parse():
@@ -420,6 +425,24 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     alg_bytes = BYTES_PER_TET * p.n_elem + BYTES_PER_VERT * p.n_vert
     achieved = alg_bytes / (tile_ms / 1000.0) / 1e9
+    if args.precision == "fp64":
+        # the FP64 HVP is bound by the FP64 pipe (1/64 of the FP32 rate), not by HBM
+        props = torch.cuda.get_device_properties(dev)
+        sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
+        peak64 = props.multi_processor_count * FP64_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
+        ach64 = FLOPS_PER_TET_FP64 * p.n_elem / (tile_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s", "frac": ach64 / peak64,
+                "traffic": None, "kernel": "k_tile_hvp<double,3>",
+                "flops_per_tet": FLOPS_PER_TET_FP64,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes "
+                               f"x 2 flops x {sm_mhz:.0f} MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(args.workload), "kernel": "k_tile_hvp<float,3>",
+                "peak_source": peak_kind}
+    roof.update({"kernel_ms": tile_ms, "kernel_launches_timed": tile_n,
+                 "kernel_timing": "CUDA event nodes around every tile launch in one profiled solve after the timed steps",
+                 "kernel_ms_back_to_back": b2b_ms})
     line = {
         "metric": "element-HVP/s (fwd Newton-CG + adjoint, whole step)",
         "value": value,
@@ -446,11 +469,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "elem-HVP/s",
                 "h2d_bytes_per_step": int(X_host.numel() * 8 + a_host.numel() * 8),
                 "d2h_bytes_per_step": int(out_g.numel() * 8 + out_x.numel() * 8)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
-                     "kernel": "k_tile_hvp<float,3>", "kernel_ms": tile_ms, "kernel_launches_timed": tile_n,
-                     "kernel_timing": "CUDA event nodes around every tile launch in one profiled solve after the timed steps",
-                     "kernel_ms_back_to_back": b2b_ms, "peak_source": peak_kind},
+        "roofline": roof,
         "clocks": clk,
     }
     if not args.no_batched:
