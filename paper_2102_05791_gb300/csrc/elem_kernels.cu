@@ -906,7 +906,6 @@ template <typename T>
 void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
 {
     hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
-    launch_cg_alpha<T>(c, c.td.n_tiles, s);
 }
 
 template <typename T>

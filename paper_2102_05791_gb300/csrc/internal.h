@@ -192,8 +192,8 @@ template <typename T>
 void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, const T *p, const T *Ap,
                            const T *hp, cudaStream_t s);
 // HVP tile kernel of the CG loop: A p for single-tile vertices, halo
-// partials, and p.Ap partials from element quadratic forms, followed by the
-// one-block reduction to alpha (no finalize).
+// partials, and p.Ap partials from element quadratic forms (no finalize; the
+// caller launches launch_cg_alpha next).
 template <typename T>
 void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>

@@ -496,9 +496,11 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
     T *d = (T *)h->vd, *r = (T *)h->vr, *p = (T *)h->vp, *Ap = (T *)h->vAp;
     h->ctx.pdl = true;  // programmatic edges between the kernels of the captured block
     for (int k = 0; k < kCgBlock; ++k) {
+        // the timing events bracket the HVP tile kernel alone
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
         launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), View<T>::a(h), p, Ap, View<T>::hp(h), s);
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k + 1], s, cudaEventRecordExternal);
+        launch_cg_alpha<T>(h->ctx, h->ctx.td.n_tiles, s);
         launch_cg_update_halo<T>(h->ctx, ph, View<T>::u(h), d, r, p, Ap, View<T>::hp(h), s);
         launch_cg_dir<T>(h->ctx, p, r, s);
     }
