@@ -29,6 +29,51 @@ static uint64_t spread2(uint64_t x)
     return x;
 }
 
+// Orders each local vertex's incidence list for the vertex phase of the tile
+// kernels, where lane j of a warp walks the list of local vertex 32w + j:
+// at every step the lanes read corner entries of the corner buffer, whose
+// shared-memory bank is the entry's word offset mod 32.  Greedily, step by
+// step, each lane takes the remaining entry whose bank the other lanes of the
+// step have used least (lanes with the fewest entries left choose first;
+// ties go to the lower offset), so the lanes of a step mostly hit distinct
+// banks.  Any fixed order gives a deterministic sum; this one is a function
+// of the tile alone.  inc: the tile's incidence block; bucket[j]..bucket[j+1]
+// is local vertex j's list.
+static void bank_order(uint16_t *inc, const std::vector<int32_t> &bucket, int nl)
+{
+    std::vector<uint16_t> src;
+    std::vector<char> taken;
+    std::vector<int> lanes;
+    for (int g0 = 0; g0 < nl; g0 += 32) {
+        const int g1 = std::min(nl, g0 + 32);
+        const int b0 = bucket[g0];
+        src.assign(inc + b0, inc + bucket[g1]);
+        taken.assign(src.size(), 0);
+        int m = 0;
+        for (int j = g0; j < g1; ++j) m = std::max(m, bucket[j + 1] - bucket[j]);
+        for (int i = 0; i < m; ++i) {
+            int used[32] = {0};
+            lanes.clear();
+            for (int j = g0; j < g1; ++j)
+                if (bucket[j + 1] - bucket[j] > i) lanes.push_back(j);
+            std::stable_sort(lanes.begin(), lanes.end(),
+                             [&](int a, int b) { return bucket[a + 1] - bucket[a] < bucket[b + 1] - bucket[b]; });
+            for (int j : lanes) {
+                int best = -1;
+                for (int q = bucket[j] - b0; q < bucket[j + 1] - b0; ++q) {
+                    if (taken[q]) continue;
+                    if (best < 0 || used[src[q] % 32] < used[src[best] % 32] ||
+                        (used[src[q] % 32] == used[src[best] % 32] && src[q] < src[best]))
+                        best = q;
+                }
+                taken[best] = 1;
+                used[src[best] % 32] += 1;
+                inc[bucket[j] + i] = src[best];
+            }
+        }
+    }
+}
+
 bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
                  int te_max, int tv_max, TileBuild &out, std::string &err)
 {
@@ -158,6 +203,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
                 out.inc[base + fill[l]++] = (uint16_t)(k * dim * out.max_te + (i - es));
             }
+        bank_order(out.inc.data() + base, bucket, nl);
         for (int j = 0; j < nl; ++j) out.lv_gid.push_back(verts[j]);
         for (int j = nl; j < nl_pad; ++j) {
             out.lv_gid.push_back(verts[0]);  // a valid id, never written
