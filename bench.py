@@ -204,10 +204,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the element-kernel source without its // comment lines: counters
-    taken on the same code stay valid across comment edits."""
-    src = os.path.join(ROOT, "paper_2102_05791_gb300", "csrc", "elem_kernels.cu")
-    lines = [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
+    """Hash of the element-kernel source and of the tile builder (which lays
+    out the kernel's inputs), without their // comment lines: counters taken
+    on the same code stay valid across comment edits."""
+    lines = []
+    for f in ("elem_kernels.cu", "tiling.cpp"):
+        src = os.path.join(ROOT, "paper_2102_05791_gb300", "csrc", f)
+        lines += [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
