@@ -74,6 +74,46 @@ static void bank_order(uint16_t *inc, const std::vector<int32_t> &bucket, int nl
     }
 }
 
+// Places the tile's incidence lists in its incidence block so that the lanes
+// of a warp load their list entries from distinct banks.  At step i lane j
+// loads the 16-bit entry first_j + i, i.e. word (first_j + i) >> 1; two lanes
+// of one warp conflict on every step both are active when their firsts agree
+// mod 64, and on every other step when they differ by 1 mod 64.  The lists
+// are laid end to end; at each position the builder places the unplaced list
+// whose warp has the fewest such conflicts with its lanes placed so far
+// (ties: longer list, then lower local id).  Returns each vertex's first
+// entry; moves the entries accordingly.  bucket[j]..bucket[j+1]: vertex j's
+// list before placement.
+static std::vector<int32_t> bank_place(uint16_t *inc, const std::vector<int32_t> &bucket, int nl)
+{
+    std::vector<int32_t> first(nl, 0);
+    std::vector<uint16_t> src(inc + bucket[0], inc + bucket[nl]);
+    std::vector<int> used(((nl + 31) / 32) * 64, 0);
+    std::vector<char> placed(nl, 0);
+    int p = 0;
+    for (int n_left = nl; n_left > 0; --n_left) {
+        const int r = p % 64;
+        int best = -1, best_score = 0;
+        for (int j = 0; j < nl; ++j) {
+            if (placed[j]) continue;
+            const int *u = &used[(j / 32) * 64];
+            const int score = 2 * u[r] + u[(r + 1) % 64] + u[(r + 63) % 64];
+            const int len = bucket[j + 1] - bucket[j], blen = best < 0 ? 0 : bucket[best + 1] - bucket[best];
+            if (best < 0 || score < best_score || (score == best_score && len > blen)) {
+                best = j;
+                best_score = score;
+            }
+        }
+        placed[best] = 1;
+        first[best] = p;
+        const int len = bucket[best + 1] - bucket[best];
+        if (len > 0) used[(best / 32) * 64 + r] += 1;
+        for (int q = 0; q < len; ++q) inc[p + q] = src[bucket[best] + q];
+        p += len;
+    }
+    return first;
+}
+
 bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
                  int te_max, int tv_max, TileBuild &out, std::string &err)
 {
@@ -194,9 +234,6 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         }
         for (int j = 0; j < nl; ++j) bucket[j + 1] += bucket[j];
         const int64_t base = (int64_t)es * nc;
-        for (int j = 0; j < nl; ++j)
-            out.lv_inc.push_back((uint32_t)bucket[j] | ((uint32_t)(bucket[j + 1] - bucket[j]) << 16) |
-                                 ((fixed && fixed[verts[j]]) ? kLvPinned : 0u));
         std::vector<int> fill(bucket.begin(), bucket.end() - 1);
         for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) {
@@ -204,6 +241,10 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
                 out.inc[base + fill[l]++] = (uint16_t)(k * dim * out.max_te + (i - es));
             }
         bank_order(out.inc.data() + base, bucket, nl);
+        const std::vector<int32_t> first = bank_place(out.inc.data() + base, bucket, nl);
+        for (int j = 0; j < nl; ++j)
+            out.lv_inc.push_back((uint32_t)first[j] | ((uint32_t)(bucket[j + 1] - bucket[j]) << 16) |
+                                 ((fixed && fixed[verts[j]]) ? kLvPinned : 0u));
         for (int j = 0; j < nl; ++j) out.lv_gid.push_back(verts[j]);
         for (int j = nl; j < nl_pad; ++j) {
             out.lv_gid.push_back(verts[0]);  // a valid id, never written
