@@ -47,20 +47,36 @@ __device__ __forceinline__ void store_corners(T *scr, int max_te, int le, const 
     }
 }
 
-// Sum of the corners touching a local vertex, in the fixed order of its
-// incidence list (inc points at the tile's incidence block, each entry the
-// corner's offset in the corner buffer; w is the vertex's lv_inc word).
+// Sum of the corners touching a local vertex in a fixed order: the entries
+// of its incidence list at even and at odd positions are summed as two
+// independent chains (two loads in flight per step), then added (inc points
+// at the tile's incidence block, each entry the corner's offset in the corner
+// buffer; w is the vertex's lv_inc word).
 template <typename T, int D>
 __device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, int max_te, T acc[D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = T(0);
     const int s0 = (int)(w & 0xffffu), n = (int)((w >> 16) & kLvCountMask);
-    for (int s = s0; s < s0 + n; ++s) {
+    T acc1[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc1[c] = T(0);
+    int s = s0;
+    for (; s + 1 < s0 + n; s += 2) {
+        const T *p = scr + inc[s], *q = scr + inc[s + 1];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            acc[c] += p[c * max_te];
+            acc1[c] += q[c * max_te];
+        }
+    }
+    if (s < s0 + n) {
         const T *p = scr + inc[s];
 #pragma unroll
         for (int c = 0; c < D; ++c) acc[c] += p[c * max_te];
     }
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] += acc1[c];
 }
 
 // Per-vertex potential terms: gravity m g y and ground penalty kc max(0,-y)^p.
