@@ -394,7 +394,7 @@ template <typename T, int D>
 struct HvpSmem {
     static constexpr int NF = D * D + D + 1;  // Dm^-1, g, W
     static constexpr int NF_SPRING = NF + D;  // + the fiber f (the spring needs q = F f)
-    size_t e, conn, a, inc, gid, code, linc, u, v, total;
+    size_t e, conn, a, inc, gid, code, linc, uv, total;
     __host__ __device__ HvpSmem(int max_te, int max_tv, int nf)
     {
         e = 16;  // two mbarriers
@@ -404,9 +404,8 @@ struct HvpSmem {
         gid = inc + (size_t)max_te * (D + 1) * 2;
         code = gid + (size_t)max_tv * 4;
         linc = code + (size_t)max_tv * 4;
-        u = linc + (size_t)max_tv * 4;
-        v = u + (size_t)max_tv * D * sizeof(T);
-        total = v + (size_t)max_tv * D * sizeof(T);
+        uv = linc + (size_t)max_tv * 4;  // [max_tv][2D]: u then v of each local vertex
+        total = uv + (size_t)max_tv * 2 * D * sizeof(T);
     }
 };
 
@@ -438,8 +437,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     const int32_t *sGid = reinterpret_cast<const int32_t *>(smem + L.gid);
     const int32_t *sCode = reinterpret_cast<const int32_t *>(smem + L.code);
     const uint32_t *sLinc = reinterpret_cast<const uint32_t *>(smem + L.linc);
-    T *su = reinterpret_cast<T *>(smem + L.u);
-    T *sv = reinterpret_cast<T *>(smem + L.v);
+    T *suv = reinterpret_cast<T *>(smem + L.uv);  // per local vertex: u (D values), then v (D values)
     const int t = blockIdx.x;
     const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
     const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
@@ -486,8 +484,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         const bool fx = (sLinc[k] & kLvPinned) != 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            su[k * D + c] = u[gid * D + c];
-            sv[k * D + c] = fx ? T(0) : v[gid * D + c];
+            suv[k * 2 * D + c] = u[gid * D + c];
+            suv[k * 2 * D + D + c] = fx ? T(0) : v[gid * D + c];
         }
     }
     if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) {
@@ -512,8 +510,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         for (int i = 0; i < D; ++i) gv[i] = sE[(FI<D>::G + i) * mte + le];
         const T W = sE[FI<D>::W * mte + le] * sel;
         const T ka = kk * sA[le];
-        edges<T, D>(su, lid, Du);
-        edges<T, D>(sv, lid, Dv);
+        edges_uv<T, D>(suv, lid, Du, Dv);
         mul<T, D>(Du, B, F, true);
         mul<T, D>(Dv, B, dF, false);
         cof<T, D>(F, C);
@@ -590,7 +587,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         if ((interior || owner) && (contact || dyn)) {
             T kcv = T(0), m = T(0), mh = T(0);  // contact curvature and inertia (+ friction) diagonals
             if (contact) {
-                const double yy = vd.X[gid * D + 1] + (double)su[k * D + 1];
+                const double yy = vd.X[gid * D + 1] + (double)suv[k * 2 * D + 1];
                 const double pen = yy < 0.0 ? -yy : 0.0;
                 const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
                 kcv = T(ph.s_el * d2);
@@ -601,13 +598,13 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             }
             T dv[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * sv[k * D + c];
+            for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * suv[k * 2 * D + D + c];
             if (interior)
 #pragma unroll
                 for (int c = 0; c < D; ++c) acc[c] += dv[c];
             if (owner)
 #pragma unroll
-                for (int c = 0; c < D; ++c) dot += dv[c] * sv[k * D + c];
+                for (int c = 0; c < D; ++c) dot += dv[c] * suv[k * 2 * D + D + c];
         }
         if (interior) {
             const bool fx = (sLinc[k] & kLvPinned) != 0;

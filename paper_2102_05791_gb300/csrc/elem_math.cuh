@@ -120,6 +120,56 @@ __device__ __forceinline__ void edges(const T *s, const int lid[D + 1], T E[D][D
     }
 }
 
+// Edge matrices of u and v from interleaved per-vertex records [u (D), v (D)]
+// with 2D*sizeof(T) bytes each: every record is read with 8- or 16-byte
+// vector loads (three float2 / double2 in 3D, one float4 or two double2 in
+// 2D) instead of 2D scalar loads.  s must be 16-byte aligned.
+template <typename T, int D>
+__device__ __forceinline__ void load_uv(const T *s, int k, T u[D], T v[D])
+{
+    if constexpr (sizeof(T) == 4 && D == 3) {
+        const float2 *r = reinterpret_cast<const float2 *>(s) + 3 * k;
+        const float2 a = r[0], b = r[1], c = r[2];
+        u[0] = a.x; u[1] = a.y; u[2] = b.x;
+        v[0] = b.y; v[1] = c.x; v[2] = c.y;
+    } else if constexpr (sizeof(T) == 4 && D == 2) {
+        const float4 a = reinterpret_cast<const float4 *>(s)[k];
+        u[0] = a.x; u[1] = a.y;
+        v[0] = a.z; v[1] = a.w;
+    } else {
+        const double2 *r = reinterpret_cast<const double2 *>(s) + D * k;
+        T w[2 * D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const double2 a = r[q];
+            w[2 * q] = a.x;
+            w[2 * q + 1] = a.y;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            u[c] = w[c];
+            v[c] = w[D + c];
+        }
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void edges_uv(const T *s, const int lid[D + 1], T Eu[D][D], T Ev[D][D])
+{
+    T u0[D], v0[D];
+    load_uv<T, D>(s, lid[0], u0, v0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T uk[D], vk[D];
+        load_uv<T, D>(s, lid[k + 1], uk, vk);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            Eu[i][k] = uk[i] - u0[i];
+            Ev[i][k] = vk[i] - v0[i];
+        }
+    }
+}
+
 // M = A B (D x D), plus the identity when add_eye.
 template <typename T, int D>
 __device__ __forceinline__ void mul(const T A[D][D], const T B[D][D], T M[D][D], bool add_eye)
