@@ -31,29 +31,39 @@
 
 namespace softsim {
 
-// Write G's columns to the corner buffer (corner-major: conflict-free stores).
+// Corner forces of one element into its record (slots corner*D + i; corner
+// 0 takes minus the column sum of G), written as pairs: 8-byte (FP32) or
+// 16-byte (FP64) stores.  rec must be aligned to the pair size.
 template <typename T, int D>
-__device__ __forceinline__ void store_corners(T *scr, int max_te, int le, const T G[D][D])
+__device__ __forceinline__ void store_corners(T *rec, const T G[D][D])
 {
+    T out[(D + 1) * D];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         T s = T(0);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            scr[((j + 1) * D + i) * max_te + le] = G[i][j];
+            out[(j + 1) * D + i] = G[i][j];
             s += G[i][j];
         }
-        scr[(0 * D + i) * max_te + le] = -s;
+        out[i] = -s;
+    }
+#pragma unroll
+    for (int q = 0; q < (D + 1) * D / 2; ++q) {
+        if constexpr (sizeof(T) == 4)
+            reinterpret_cast<float2 *>(rec)[q] = make_float2(out[2 * q], out[2 * q + 1]);
+        else
+            reinterpret_cast<double2 *>(rec)[q] = make_double2(out[2 * q], out[2 * q + 1]);
     }
 }
 
 // Sum of the corners touching a local vertex in a fixed order: the entries
 // of its incidence list at even and at odd positions are summed as two
 // independent chains (two loads in flight per step), then added (inc points
-// at the tile's incidence block, each entry the corner's offset in the corner
-// buffer; w is the vertex's lv_inc word).
+// at the tile's incidence block, each entry the offset of a corner's D
+// values among the tile's element records; w is the vertex's lv_inc word).
 template <typename T, int D>
-__device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, int max_te, T acc[D])
+__device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, T acc[D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = T(0);
@@ -66,14 +76,14 @@ __device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, 
         const T *p = scr + inc[s], *q = scr + inc[s + 1];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            acc[c] += p[c * max_te];
-            acc1[c] += q[c * max_te];
+            acc[c] += p[c];
+            acc1[c] += q[c];
         }
     }
     if (s < s0 + n) {
         const T *p = scr + inc[s];
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] += p[c * max_te];
+        for (int c = 0; c < D; ++c) acc[c] += p[c];
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] += acc1[c];
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
                 for (int k = 0; k < D; ++k) s += (mu * F[i][k] + cc * C[i][k]) * B[j][k];
                 G[i][j] = W * (s + ka * Ff[i] * gv[j]);
             }
-        store_corners<double, D>(scr, td.max_te, le, G);
+        store_corners<double, D>(scr + (int64_t)le * td.rs, G);
     }
     __syncthreads();
     double gn2 = 0.0;
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
         const int code = td.lv_code[vs + k];
         if (code == LV_PAD) continue;
         double acc[D];
-        gather_corners<double, D>(tinc, td.lv_inc[vs + k], scr, td.max_te, acc);
+        gather_corners<double, D>(tinc, td.lv_inc[vs + k], scr, acc);
         const int64_t gid = td.lv_gid[vs + k];
         if (code == LV_INTERIOR) {
             const double m = vd.mass[gid];
@@ -389,18 +399,16 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
 // ---------------------------------------------------------------- HVP
 
 // Shared-memory plan of the HVP tile kernel (offsets in bytes, all 16-byte
-// aligned because max_te is a multiple of 8 and max_tv of 4).
+// aligned because max_te is a multiple of 8, max_tv of 4 and rs even).
 template <typename T, int D>
 struct HvpSmem {
-    static constexpr int NF = D * D + D + 1;  // Dm^-1, g, W
-    static constexpr int NF_SPRING = NF + D;  // + the fiber f (the spring needs q = F f)
-    size_t e, conn, a, inc, gid, code, linc, uv, total;
-    __host__ __device__ HvpSmem(int max_te, int max_tv, int nf)
+    size_t e, rec, conn, inc, gid, code, linc, uv, total;
+    __host__ __device__ HvpSmem(int max_te, int max_tv, int rs)
     {
         e = 16;  // two mbarriers
-        conn = e + (size_t)nf * max_te * sizeof(T);
-        a = conn + (size_t)max_te * 4;
-        inc = a + (size_t)max_te * sizeof(T);
+        rec = e;  // [max_te][rs] element records
+        conn = rec + (size_t)rs * max_te * sizeof(T);
+        inc = conn + (size_t)max_te * 4;
         gid = inc + (size_t)max_te * (D + 1) * 2;
         code = gid + (size_t)max_tv * 4;
         linc = code + (size_t)max_tv * 4;
@@ -409,30 +417,30 @@ struct HvpSmem {
     }
 };
 
-// HVP of one tile per CTA.  Thread 0 pulls the tile's element fields,
-// connectivity, activations, incidence lists and local-vertex tables into
-// shared memory with bulk copies on one mbarrier; the tile's vertex values
-// are then gathered, each thread evaluates dP(dF) for its elements from
-// shared memory, the per-corner forces overwrite the element fields in place
-// (the corner array needs (D+1)*D <= NF columns per element), and one thread
+// HVP of one tile per CTA.  Thread 0 pulls the tile's element records
+// (fields and activation), connectivity, incidence lists and local-vertex
+// tables into shared memory with bulk copies on two mbarriers; the tile's
+// vertex values are then gathered, each thread evaluates dP(dF) for its
+// elements from their records (pair loads), the element's corner forces
+// overwrite its own record in place ((D+1)*D <= RS slots), and one thread
 // per local vertex adds its corners in fixed order.
 // SPRING selects the active-spring muscle at compile time, so the
 // contractile kernel carries none of its code or its extra fields.
 template <typename T, int D, bool CG, int MINB, int MTE, bool SPRING>
-__global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> ed, VertDev vd, Phys ph,
-                                                  const T *__restrict__ u, const T *__restrict__ a,
-                                                  const T *__restrict__ v, T *__restrict__ y, T *__restrict__ hp,
+__global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__restrict__ erec, VertDev vd,
+                                                  Phys ph, const T *__restrict__ u, const T *__restrict__ v,
+                                                  T *__restrict__ y, T *__restrict__ hp,
                                                   double *__restrict__ partials, DevScalars *__restrict__ sc)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // MTE != 0: the tile capacity is a compile-time constant, so every
-    // element-field and corner offset below folds into an immediate
-    constexpr int NF = SPRING ? HvpSmem<T, D>::NF_SPRING : HvpSmem<T, D>::NF;
-    const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv, NF);
+    // record and corner offset below folds into an immediate
+    constexpr int NF = hvp_fields(D, SPRING);
+    constexpr int RS = rec_stride(NF);  // record: NF fields, the activation at slot NF, padding
+    const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv, RS);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
-    T *sE = reinterpret_cast<T *>(smem + L.e);
+    T *sRec = reinterpret_cast<T *>(smem + L.rec);
     const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
-    const T *sA = reinterpret_cast<const T *>(smem + L.a);
     const uint16_t *sInc = reinterpret_cast<const uint16_t *>(smem + L.inc);
     const int32_t *sGid = reinterpret_cast<const int32_t *>(smem + L.gid);
     const int32_t *sCode = reinterpret_cast<const int32_t *>(smem + L.code);
@@ -441,7 +449,6 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     const int t = blockIdx.x;
     const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
     const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
-    const int mte = MTE ? MTE : td.max_te;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
@@ -450,13 +457,11 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         bulk_g2s(smem + L.gid, td.lv_gid + vs, (uint32_t)nlv * 4, bar);
         bulk_g2s(smem + L.code, td.lv_code + vs, (uint32_t)nlv * 4, bar);
         bulk_g2s(smem + L.linc, td.lv_inc + vs, (uint32_t)nlv * 4, bar);
-        const uint32_t be = (uint32_t)ne_t * sizeof(T);
-        mbar_arrive_expect_tx(bar + 1, NF * be + (uint32_t)ne_t * 4 + be + (uint32_t)ne_t * (D + 1) * 2);
+        const uint32_t brec = (uint32_t)ne_t * RS * sizeof(T);
+        mbar_arrive_expect_tx(bar + 1, brec + (uint32_t)ne_t * 4 + (uint32_t)ne_t * (D + 1) * 2);
         const uint64_t pol = l2_evict_first_policy();  // element data is read once per launch
-#pragma unroll
-        for (int f = 0; f < NF; ++f) bulk_g2s_stream(sE + (size_t)f * mte, ed.field(f) + es, be, bar + 1, pol);
+        bulk_g2s_stream(sRec, erec + (int64_t)es * RS, brec, bar + 1, pol);
         bulk_g2s_stream(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar + 1, pol);
-        bulk_g2s_stream(smem + L.a, a + es, be, bar + 1, pol);
         bulk_g2s_stream(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1, pol);
     }
     __syncthreads();
@@ -501,15 +506,19 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
         int lid[D + 1];
         unpack<D>(sConn[le], lid);
+        // Dm^-1, g and W first (for the contractile muscle that includes the
+        // activation); the spring's fiber and activation where they are used
+        constexpr int N1 = (FI<D>::W + 2) / 2 * 2;
+        T rv[RS];
+        load_pairs<T, N1>(sRec + le * RS, rv);
         T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D], gv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
-            for (int j = 0; j < D; ++j) B[i][j] = sE[(FI<D>::B + i * D + j) * mte + le];
+            for (int j = 0; j < D; ++j) B[i][j] = rv[FI<D>::B + i * D + j];
 #pragma unroll
-        for (int i = 0; i < D; ++i) gv[i] = sE[(FI<D>::G + i) * mte + le];
-        const T W = sE[FI<D>::W * mte + le] * sel;
-        const T ka = kk * sA[le];
+        for (int i = 0; i < D; ++i) gv[i] = rv[FI<D>::G + i];
+        const T W = rv[FI<D>::W] * sel;
         edges_uv<T, D>(suv, lid, Du, Dv);
         mul<T, D>(Du, B, F, true);
         mul<T, D>(Dv, B, dF, false);
@@ -532,11 +541,13 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
             for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
             dvg[i] = s;
         }
+        if constexpr (N1 < RS) load_pairs<T, RS - N1>(sRec + le * RS + N1, rv + N1);
+        const T aval = rv[NF];
         if constexpr (SPRING) {  // spring, with q = F f = f + Du g
             T q[D], s2 = T(0), qdq = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                T s = sE[(FI<D>::F + i) * mte + le];
+                T s = rv[FI<D>::F + i];
 #pragma unroll
                 for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
                 q[i] = s;
@@ -544,12 +555,12 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
                 qdq += s * dvg[i];
             }
             T c1, c2;
-            spring_terms<T>(W != T(0), kk, sA[le], sqrt(s2), c1, c2);
+            spring_terms<T>(W != T(0), kk, aval, sqrt(s2), c1, c2);
 #pragma unroll
             for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
         } else {
 #pragma unroll
-            for (int i = 0; i < D; ++i) dvg[i] *= ka;
+            for (int i = 0; i < D; ++i) dvg[i] *= kk * aval;
         }
         T G[D][D];
 #pragma unroll
@@ -568,7 +579,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
 #pragma unroll
                 for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
         }
-        store_corners<T, D>(sE, mte, le, G);  // overwrites this element's own columns only
+        store_corners<T, D>(sRec + le * RS, G);  // overwrites this element's own record only
     }
     __syncthreads();
     // p.Ap of this thread in the kernel's precision: in the mixed kernel the
@@ -580,7 +591,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, ElemDev<T> e
         const int code = sCode[k];
         if (code == LV_PAD) continue;
         T acc[D];
-        gather_corners<T, D>(sInc, sLinc[k], sE, mte, acc);
+        gather_corners<T, D>(sInc, sLinc[k], sRec, acc);
         const int64_t gid = sGid[k];
         const bool interior = code == LV_INTERIOR;
         const bool owner = CG && (interior || (code & 1));  // counts the vertex terms of p.Ap
@@ -825,7 +836,7 @@ void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uh
                  double *hp, cudaStream_t s)
 {
     c.n_launch += 2;
-    const size_t sm = smem_verts(c, sizeof(double), 1) + (size_t)c.td.max_te * (c.dim + 1) * c.dim * sizeof(double);
+    const size_t sm = smem_verts(c, sizeof(double), 1) + (size_t)c.td.max_te * c.td.rs * sizeof(double);
     const int fb = c.n_fin_blocks;
     if (c.dim == 2) {
         k_tile_grad<2><<<c.td.n_tiles, c.threads, sm, s>>>(c.td, c.e64, c.vd, ph, u, uhat, a, g, hp, c.partials);
@@ -837,19 +848,17 @@ void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uh
 }
 
 template <typename T>
-static const ElemDev<T> &edev(const Ctx &c);
+static const T *erec(const Ctx &c);
 template <>
-const ElemDev<float> &edev<float>(const Ctx &c) { return c.e32; }
+const float *erec<float>(const Ctx &c) { return c.rec32; }
 template <>
-const ElemDev<double> &edev<double>(const Ctx &c) { return c.e64; }
+const double *erec<double>(const Ctx &c) { return c.rec64; }
 
 template <typename T>
 size_t hvp_smem(const Ctx &c)
 {
-    const int nf2 = c.muscle ? HvpSmem<T, 2>::NF_SPRING : HvpSmem<T, 2>::NF;
-    const int nf3 = c.muscle ? HvpSmem<T, 3>::NF_SPRING : HvpSmem<T, 3>::NF;
-    return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv, nf2).total
-                      : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv, nf3).total;
+    return c.dim == 2 ? HvpSmem<T, 2>(c.td.max_te, c.td.max_tv, c.td.rs).total
+                      : HvpSmem<T, 3>(c.td.max_te, c.td.max_tv, c.td.rs).total;
 }
 
 // Resident CTAs per SM that the tile's shared memory allows (at most 4);
@@ -866,35 +875,35 @@ int hvp_blocks_per_sm(const Ctx &c)
 constexpr int kCap2 = 512, kCap3 = 384;
 
 template <typename T, int D, bool CG, int MINB>
-static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+static void hvp_tile_v(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s)
 {
     constexpr int CAP = D == 2 ? kCap2 : kCap3;
     if (c.muscle)  // the spring variant exists for the runtime tile capacity only
         launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0, true>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s,
-                 c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+                 c.td, erec<T>(c), c.vd, ph, u, v, y, hp, c.partials, c.sc);
     else if (sizeof(T) == 4 && c.td.max_te == CAP)
         launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, (sizeof(T) == 4 ? CAP : 0), false>, dim3(c.td.n_tiles),
-                 dim3(c.threads), hvp_smem<T>(c), s, c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+                 dim3(c.threads), hvp_smem<T>(c), s, c.td, erec<T>(c), c.vd, ph, u, v, y, hp, c.partials, c.sc);
     else
         launch_k(c.pdl, k_tile_hvp<T, D, CG, MINB, 0, false>, dim3(c.td.n_tiles), dim3(c.threads), hvp_smem<T>(c), s,
-                 c.td, edev<T>(c), c.vd, ph, u, a, v, y, hp, c.partials, c.sc);
+                 c.td, erec<T>(c), c.vd, ph, u, v, y, hp, c.partials, c.sc);
 }
 
 template <typename T, bool CG>
-static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s)
 {
     c.n_launch += 1;
     const int b = hvp_blocks_per_sm<T>(c);
     if constexpr (sizeof(T) == 4) {
         if (c.dim == 2)
-            (b >= 4 ? hvp_tile_v<T, 2, CG, 4> : hvp_tile_v<T, 2, CG, 3>)(c, ph, u, a, v, y, hp, s);
+            (b >= 4 ? hvp_tile_v<T, 2, CG, 4> : hvp_tile_v<T, 2, CG, 3>)(c, ph, u, v, y, hp, s);
         else
-            (b >= 4 ? hvp_tile_v<T, 3, CG, 4> : hvp_tile_v<T, 3, CG, 3>)(c, ph, u, a, v, y, hp, s);
+            (b >= 4 ? hvp_tile_v<T, 3, CG, 4> : hvp_tile_v<T, 3, CG, 3>)(c, ph, u, v, y, hp, s);
     } else {
         if (c.dim == 2)
-            (b >= 2 ? hvp_tile_v<T, 2, CG, 2> : hvp_tile_v<T, 2, CG, 1>)(c, ph, u, a, v, y, hp, s);
+            (b >= 2 ? hvp_tile_v<T, 2, CG, 2> : hvp_tile_v<T, 2, CG, 1>)(c, ph, u, v, y, hp, s);
         else
-            (b >= 2 ? hvp_tile_v<T, 3, CG, 2> : hvp_tile_v<T, 3, CG, 1>)(c, ph, u, a, v, y, hp, s);
+            (b >= 2 ? hvp_tile_v<T, 3, CG, 2> : hvp_tile_v<T, 3, CG, 1>)(c, ph, u, v, y, hp, s);
     }
 }
 
@@ -909,23 +918,22 @@ static void hvp_fin(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, 
 }
 
 template <typename T>
-void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s)
 {
-    hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
+    hvp_tile<T, false>(c, ph, u, v, y, hp, s);
     hvp_fin<T>(c, ph, u, v, y, hp, s);
 }
 
 template <typename T>
-void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s)
+void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s)
 {
-    hvp_tile<T, true>(c, ph, u, a, v, y, hp, s);
+    hvp_tile<T, true>(c, ph, u, v, y, hp, s);
 }
 
 template <typename T>
-void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
-                          cudaStream_t s)
+void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s)
 {
-    hvp_tile<T, false>(c, ph, u, a, v, y, hp, s);
+    hvp_tile<T, false>(c, ph, u, v, y, hp, s);
 }
 
 template <typename T>
@@ -995,18 +1003,18 @@ cudaError_t configure_elem_kernels()
     return e;
 }
 
-template void launch_hvp<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
-                                float *, cudaStream_t);
-template void launch_hvp<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
-                                 double *, double *, cudaStream_t);
-template void launch_hvp_cg<float>(const Ctx &, const Phys &, const float *, const float *, const float *, float *,
-                                   float *, cudaStream_t);
-template void launch_hvp_cg<double>(const Ctx &, const Phys &, const double *, const double *, const double *,
-                                    double *, double *, cudaStream_t);
-template void launch_hvp_tile_only<float>(const Ctx &, const Phys &, const float *, const float *, const float *,
-                                          float *, float *, cudaStream_t);
-template void launch_hvp_tile_only<double>(const Ctx &, const Phys &, const double *, const double *,
-                                           const double *, double *, double *, cudaStream_t);
+template void launch_hvp<float>(const Ctx &, const Phys &, const float *, const float *, float *, float *,
+                                cudaStream_t);
+template void launch_hvp<double>(const Ctx &, const Phys &, const double *, const double *, double *, double *,
+                                 cudaStream_t);
+template void launch_hvp_cg<float>(const Ctx &, const Phys &, const float *, const float *, float *, float *,
+                                   cudaStream_t);
+template void launch_hvp_cg<double>(const Ctx &, const Phys &, const double *, const double *, double *, double *,
+                                    cudaStream_t);
+template void launch_hvp_tile_only<float>(const Ctx &, const Phys &, const float *, const float *, float *, float *,
+                                          cudaStream_t);
+template void launch_hvp_tile_only<double>(const Ctx &, const Phys &, const double *, const double *, double *,
+                                           double *, cudaStream_t);
 template void launch_hvp_finalize_only<float>(const Ctx &, const Phys &, const float *, const float *, float *,
                                               const float *, cudaStream_t);
 template void launch_hvp_finalize_only<double>(const Ctx &, const Phys &, const double *, const double *,

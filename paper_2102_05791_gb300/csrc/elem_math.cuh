@@ -120,6 +120,26 @@ __device__ __forceinline__ void edges(const T *s, const int lid[D + 1], T E[D][D
     }
 }
 
+// The N words of a record (N even, record aligned to a pair) with pair
+// loads: 8-byte in FP32, 16-byte in FP64.
+template <typename T, int N>
+__device__ __forceinline__ void load_pairs(const T *r, T out[N])
+{
+    static_assert(N % 2 == 0, "records are read in pairs");
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 p = reinterpret_cast<const float2 *>(r)[q];
+            out[2 * q] = p.x;
+            out[2 * q + 1] = p.y;
+        } else {
+            const double2 p = reinterpret_cast<const double2 *>(r)[q];
+            out[2 * q] = p.x;
+            out[2 * q + 1] = p.y;
+        }
+    }
+}
+
 // Edge matrices of u and v from interleaved per-vertex records [u (D), v (D)]
 // with 2D*sizeof(T) bytes each: every record is read with 8- or 16-byte
 // vector loads (three float2 / double2 in 3D, one float4 or two double2 in

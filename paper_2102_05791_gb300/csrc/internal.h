@@ -41,11 +41,14 @@ struct TileDev {
     int n_tiles = 0;
     int max_te = 0, max_tv = 0;
     int n_fin = 0;
+    int rs = 0;                          // element-record stride (words), rec_stride(hvp_fields(dim, spring))
     const int32_t *tile_elem = nullptr;  // [n_tiles + 1]
     const int32_t *tile_vert = nullptr;  // [n_tiles + 1]
     const int32_t *lv_gid = nullptr;     // [n_lv]
     const int32_t *lv_code = nullptr;    // [n_lv]
-    const uint32_t *lv_inc = nullptr;    // [n_lv] first incidence (within the tile) | count << 16
+    const uint32_t *lv_inc = nullptr;    // [n_lv] first incidence (within the tile) | count << 16 | pinned
+    // inc entries: the offset of a corner's dim values among the tile's element
+    // records, local element * rs + corner * dim
     const uint16_t *inc = nullptr;       // [ne_int * (dim+1)]
     const uint32_t *conn = nullptr;      // [ne_int]
     const int32_t *perm = nullptr;       // [ne_int] tile order -> caller order, -1 = padding
@@ -134,7 +137,10 @@ struct Ctx {
     TileDev td;
     VertDev vd;
     ElemDev<double> e64;
-    ElemDev<float> e32;
+    // HVP element records [ne_int][td.rs] in tile order: the hvp_fields()
+    // element fields, then the activation (written by set_activation)
+    float *rec32 = nullptr;   // mixed precision only
+    double *rec64 = nullptr;
     int threads = 256;
     int muscle = 0;              // muscle model (the spring's HVP also stages the fiber)
     double *partials = nullptr;  // [n_partials] FP64 block partial sums
@@ -159,13 +165,12 @@ void launch_energy(const Ctx &c, const Phys &ph, const double *u, const double *
 void launch_grad(const Ctx &c, const Phys &ph, const double *u, const double *uhat,
                  const double *a, double *g, double *hp, cudaStream_t s);
 
-// HVP y = A v (A = H, or M + dt^2 H when ph.dyn), masked.
+// HVP y = A v (A = H, or M + dt^2 H when ph.dyn), masked; the activations
+// come from the element records.
 template <typename T>
-void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp,
-                cudaStream_t s);
+void launch_hvp(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>
-void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y,
-                          T *hp, cudaStream_t s);
+void launch_hvp_tile_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>
 void launch_hvp_finalize_only(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y,
                               const T *hp, cudaStream_t s);
@@ -195,7 +200,7 @@ void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r,
 // partials, and p.Ap partials from element quadratic forms (no finalize; the
 // caller launches launch_cg_alpha next).
 template <typename T>
-void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *a, const T *v, T *y, T *hp, cudaStream_t s);
+void launch_hvp_cg(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y, T *hp, cudaStream_t s);
 template <typename T>
 void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s);
 template <typename T>
@@ -209,7 +214,8 @@ void launch_u_to_x(const Ctx &c, const double *u, double *x, cudaStream_t s);
 void launch_uhat(const Ctx &c, const double *x0, const double *v0, double dt, double *uhat,
                  cudaStream_t s);
 template <typename T>
-void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s);
+// internal[e * stride] = user[perm[e]] (0 for padding elements), e in tile order
+void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s, int64_t stride = 1);
 template <typename Tin, typename Tout>
 void launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
 void launch_mask_copy(const Ctx &c, const double *in, double *out, cudaStream_t s);

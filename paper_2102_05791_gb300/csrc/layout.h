@@ -14,4 +14,18 @@ constexpr int32_t LV_PAD = -2;        // padding entry
 constexpr uint32_t kLvPinned = 0x80000000u;
 constexpr uint32_t kLvCountMask = 0x7fffu;
 
+// Element record of the HVP tile kernels: the nf element fields (Dm^-1, g, W,
+// and the fiber f with the spring muscle) followed by the activation a,
+// padded to a stride of 2 mod 4 words so that the pair loads of a warp's
+// records (8 bytes in FP32, 16 in FP64) fall in distinct banks.  In shared
+// memory the same record later holds the element's (d+1)*d corner forces.
+#ifdef __CUDACC__
+#define SOFTSIM_HD __host__ __device__
+#else
+#define SOFTSIM_HD
+#endif
+SOFTSIM_HD constexpr int hvp_fields(int dim, bool spring) { return dim * dim + dim + 1 + (spring ? dim : 0); }
+SOFTSIM_HD constexpr int rec_stride(int nf) { return nf + 1 + ((2 - (nf + 1) % 4) + 4) % 4; }
+#undef SOFTSIM_HD
+
 }  // namespace softsim

@@ -46,7 +46,7 @@ struct sim_handle {
     uint8_t *fixed = nullptr;
     double *u = nullptr, *uhat = nullptr, *g = nullptr, *hp64 = nullptr, *a64 = nullptr;
     double *fw = nullptr, *u0 = nullptr;  // ground friction of the current step (null when off)
-    float *u32 = nullptr, *a32 = nullptr, *hp32 = nullptr;
+    float *u32 = nullptr, *hp32 = nullptr;
     void *vd = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr;  // CG vectors in the HVP precision
     double *work = nullptr, *lam = nullptr, *lacc = nullptr, *r64 = nullptr, *Hx = nullptr;
     int verbose = 0;
@@ -268,8 +268,10 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
 
     // --- tiles
     int te = h->opt.tile_elems > 0 ? h->opt.tile_elems : (d == 3 ? 384 : 512);
+    const int nf_hvp = hvp_fields(d, h->mat.muscle_model == SIM_MUSCLE_SPRING);
+    const int rs = rec_stride(nf_hvp);
     std::string terr;
-    if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, mesh->fixed, te, kMaxTileVerts, h->tb, terr))
+    if (!build_tiles(d, nv, ne, mesh->rest_pos, mesh->elems, mesh->fixed, te, kMaxTileVerts, rs, h->tb, terr))
         return fail(h, SIM_EINVAL, "tiling: " + terr);
     const TileBuild &tb = h->tb;
     const int64_t ne_int = tb.ne_int;
@@ -336,12 +338,20 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     c.ne_int = ne_int;
     c.e64.base = ce64;
     c.e64.stride = ne_int;
-    if (is_mixed(h)) {
-        std::vector<float> e32(edata.begin(), edata.end());
-        const float *ce32;
-        if ((rc = upload(h, e32, &ce32))) return rc;
-        c.e32.base = ce32;
-        c.e32.stride = ne_int;
+    {
+        // HVP records: the first nf_hvp fields in the FI order, activation slot and padding zero
+        std::vector<double> rec((size_t)rs * ne_int, 0.0);
+        for (int64_t i = 0; i < ne_int; ++i)
+            for (int f = 0; f < nf_hvp; ++f) rec[(size_t)i * rs + f] = edata[(size_t)f * ne_int + i];
+        const double *cr64;
+        if ((rc = upload(h, rec, &cr64))) return rc;
+        c.rec64 = const_cast<double *>(cr64);
+        if (is_mixed(h)) {
+            std::vector<float> rec32(rec.begin(), rec.end());
+            const float *cr32;
+            if ((rc = upload(h, rec32, &cr32))) return rc;
+            c.rec32 = const_cast<float *>(cr32);
+        }
     }
     c.vd.nv = nv;
     c.vd.X = h->X;
@@ -352,6 +362,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     td.max_te = tb.max_te;
     td.max_tv = tb.max_tv;
     td.n_fin = (int)tb.fin_gid.size();
+    td.rs = tb.rs;
     if ((rc = upload(h, tb.tile_elem, &td.tile_elem))) return rc;
     if ((rc = upload(h, tb.tile_vert, &td.tile_vert))) return rc;
     if ((rc = upload(h, tb.lv_gid, &td.lv_gid))) return rc;
@@ -391,11 +402,10 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     h->vAp = dalloc(h, vbytes * nd);
     if (is_mixed(h)) {
         h->u32 = (float *)dalloc(h, sizeof(float) * nd);
-        h->a32 = (float *)dalloc(h, sizeof(float) * ne_int);
         h->hp32 = (float *)dalloc(h, sizeof(float) * std::max<int64_t>(tb.n_slots, 1) * d);
     }
     if (!c.partials || !h->sc || !h->u || !h->uhat || !h->g || !h->work || !h->lam || !h->lacc || !h->r64 || !h->Hx || !h->hp64 || !h->a64 || !h->vd ||
-        !h->vr || !h->vp || !h->vAp || (is_mixed(h) && (!h->u32 || !h->a32 || !h->hp32)))
+        !h->vr || !h->vp || !h->vAp || (is_mixed(h) && (!h->u32 || !h->hp32)))
         return fail(h, SIM_ENOMEM, "device allocation failed");
     CK(h, cudaMemset(h->sc, 0, sizeof(DevScalars)));
     CK(h, cudaMemset(h->u, 0, sizeof(double) * nd));
@@ -461,21 +471,22 @@ struct View;
 template <>
 struct View<float> {
     static float *u(sim_handle *h) { return h->u32; }
-    static float *a(sim_handle *h) { return h->a32; }
     static float *hp(sim_handle *h) { return h->hp32; }
 };
 template <>
 struct View<double> {
     static double *u(sim_handle *h) { return h->u; }
-    static double *a(sim_handle *h) { return h->a64; }
     static double *hp(sim_handle *h) { return h->hp64; }
 };
 
 // Set the internal activation copies from the caller's array.
 static int set_activation(sim_handle *h, const double *a, cudaStream_t s)
 {
-    launch_gather_elem<double>(h->ctx, a, h->a64, s);
-    if (is_mixed(h)) launch_gather_elem<float>(h->ctx, a, h->a32, s);
+    const Ctx &c = h->ctx;
+    const int slot = hvp_fields(c.dim, c.muscle == SIM_MUSCLE_SPRING);  // after the HVP fields
+    launch_gather_elem<double>(c, a, h->a64, s);
+    launch_gather_elem<double>(c, a, c.rec64 + slot, s, c.td.rs);
+    if (is_mixed(h)) launch_gather_elem<float>(c, a, c.rec32 + slot, s, c.td.rs);
     CKL(h);
     return SIM_OK;
 }
@@ -498,7 +509,7 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
     for (int k = 0; k < kCgBlock; ++k) {
         // the timing events bracket the HVP tile kernel alone
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
-        launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), View<T>::a(h), p, Ap, View<T>::hp(h), s);
+        launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k + 1], s, cudaEventRecordExternal);
         launch_cg_alpha<T>(h->ctx, h->ctx.td.n_tiles, s);
         launch_cg_update_halo<T>(h->ctx, ph, View<T>::u(h), d, r, p, Ap, View<T>::hp(h), s);
@@ -717,7 +728,7 @@ static int adjoint_impl(sim_handle *h, bool dyn, const double *b, double *lambda
         S.cg_iters_total += it;
         budget -= std::max(it, 1);
         launch_accumulate<T>(c, h->lacc, (const T *)h->vd, s);
-        launch_hvp<double>(c, ph, h->u, h->a64, h->lacc, h->Hx, h->hp64, s);
+        launch_hvp<double>(c, ph, h->u, h->lacc, h->Hx, h->hp64, s);
         launch_residual(c, h->work, h->Hx, h->r64, s);
         CKL(h);
         if ((rc = read_scalars(h, s))) return rc;
@@ -779,9 +790,9 @@ extern "C" int sim_hvp(sim_handle *h, const double *x, const double *a, const vo
     if ((rc = set_activation(h, a, s))) return rc;
     const Phys ph = make_phys(h, false);
     if (is_mixed(h))
-        launch_hvp<float>(h->ctx, ph, h->u32, h->a32, (const float *)v, (float *)Hv, h->hp32, s);
+        launch_hvp<float>(h->ctx, ph, h->u32, (const float *)v, (float *)Hv, h->hp32, s);
     else
-        launch_hvp<double>(h->ctx, ph, h->u, h->a64, (const double *)v, (double *)Hv, h->hp64, s);
+        launch_hvp<double>(h->ctx, ph, h->u, (const double *)v, (double *)Hv, h->hp64, s);
     CKL(h);
     return SIM_OK;
 }
@@ -1059,9 +1070,9 @@ extern "C" int sim_time_hvp(sim_handle *h, int n, float *ms, void *stream)
     CK(h, cudaEventRecord(h->ev0, s));
     for (int i = 0; i < n; ++i) {
         if (is_mixed(h))
-            launch_hvp_tile_only<float>(h->ctx, ph, h->u32, h->a32, (const float *)h->vp, (float *)h->vAp, h->hp32, s);
+            launch_hvp_tile_only<float>(h->ctx, ph, h->u32, (const float *)h->vp, (float *)h->vAp, h->hp32, s);
         else
-            launch_hvp_tile_only<double>(h->ctx, ph, h->u, h->a64, (const double *)h->vp, (double *)h->vAp, h->hp64, s);
+            launch_hvp_tile_only<double>(h->ctx, ph, h->u, (const double *)h->vp, (double *)h->vAp, h->hp64, s);
     }
     CK(h, cudaEventRecord(h->ev1, s));
     CKL(h);

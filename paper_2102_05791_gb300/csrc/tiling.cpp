@@ -115,7 +115,7 @@ static std::vector<int32_t> bank_place(uint16_t *inc, const std::vector<int32_t>
 }
 
 bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
-                 int te_max, int tv_max, TileBuild &out, std::string &err)
+                 int te_max, int tv_max, int rec_stride, TileBuild &out, std::string &err)
 {
     const int nc = dim + 1;
     out = TileBuild();
@@ -124,7 +124,12 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     out.ne = ne;
     if (tv_max > 256) tv_max = 256;
     if (te_max < 1) te_max = 1;
-    if (te_max * nc > 65535) te_max = 65535 / nc;
+    if (rec_stride < nc * dim) {
+        err = "element record stride too small for the corner forces";
+        return false;
+    }
+    out.rs = rec_stride;
+    if ((int64_t)te_max * rec_stride > 65535) te_max = 65535 / rec_stride / kElemPad * kElemPad;
 
     // --- Morton order of element centroids, quantised at the mean element size
     std::vector<double> lo(dim, INFINITY), hi(dim, -INFINITY);
@@ -194,7 +199,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     out.ne_int = out.tile_elem.back();
     for (int ti = 0; ti < out.n_tiles; ++ti)
         out.max_te = std::max(out.max_te, out.tile_elem[ti + 1] - out.tile_elem[ti]);
-    if ((int64_t)(dim + 1) * dim * out.max_te > 65535) {
+    if ((int64_t)out.max_te * rec_stride > 65535) {
         err = "tile too large for 16-bit corner offsets";
         return false;
     }
@@ -238,7 +243,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) {
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
-                out.inc[base + fill[l]++] = (uint16_t)(k * dim * out.max_te + (i - es));
+                out.inc[base + fill[l]++] = (uint16_t)((i - es) * rec_stride + k * dim);
             }
         bank_order(out.inc.data() + base, bucket, nl);
         const std::vector<int32_t> first = bank_place(out.inc.data() + base, bucket, nl);

@@ -246,11 +246,11 @@ __global__ void k_uhat(int64_t n, const double *__restrict__ x0, const double *_
 
 template <typename T>
 __global__ void k_gather_elem(int64_t ne_int, const int32_t *__restrict__ perm, const double *__restrict__ user,
-                              T *__restrict__ internal)
+                              T *__restrict__ internal, int64_t stride)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne_int; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t pe = perm[e];
-        internal[e] = pe >= 0 ? T(user[pe]) : T(0);
+        internal[e * stride] = pe >= 0 ? T(user[pe]) : T(0);
     }
 }
 
@@ -443,10 +443,10 @@ void launch_uhat(const Ctx &c, const double *x0, const double *v0, double dt, do
 }
 
 template <typename T>
-void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s)
+void launch_gather_elem(const Ctx &c, const double *user, T *internal, cudaStream_t s, int64_t stride)
 {
     c.n_launch += 1;
-    k_gather_elem<T><<<vec_grid(c.ne_int), 256, 0, s>>>(c.ne_int, c.td.perm, user, internal);
+    k_gather_elem<T><<<vec_grid(c.ne_int), 256, 0, s>>>(c.ne_int, c.td.perm, user, internal, stride);
 }
 
 template <typename Tin, typename Tout>
@@ -497,7 +497,7 @@ int vec_grid_size(int64_t n) { return vec_grid(n); }
     template void launch_cg_alpha<T>(const Ctx &, int, cudaStream_t);                                               \
     template void launch_dir_check<T>(const Ctx &, const double *, T *, cudaStream_t);                              \
     template void launch_step_update<T>(const Ctx &, double *, const T *, double, float *, cudaStream_t);           \
-    template void launch_gather_elem<T>(const Ctx &, const double *, T *, cudaStream_t);                            \
+    template void launch_gather_elem<T>(const Ctx &, const double *, T *, cudaStream_t, int64_t);                   \
     template void launch_accumulate<T>(const Ctx &, double *, const T *, cudaStream_t);
 INST(float)
 INST(double)

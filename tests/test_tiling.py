@@ -24,7 +24,8 @@ def lib(tmp_path_factory):
                    check=True)
     L = C.CDLL(out)
     vp = C.c_void_p
-    L.tb_build.argtypes = [C.c_int, C.c_int64, C.c_int64, vp, vp, vp, C.c_int, C.c_int, C.c_char_p, C.c_int]
+    L.tb_build.argtypes = [C.c_int, C.c_int64, C.c_int64, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_char_p,
+                           C.c_int]
     L.tb_build.restype = vp
     L.tb_free.argtypes = [vp]
     L.tb_scalar.argtypes = [vp, C.c_int]
@@ -49,12 +50,23 @@ def tile_lists(t, ti, nc):
     return [inc[first[k]:first[k] + count[k]] for k in range(ve - vs)]
 
 
-def build(L, p, te, tv=256):
+def rec_stride(dim, spring=False):
+    """Element-record stride of the HVP kernels: the element fields (Dm^-1, g,
+    W, and f with the spring muscle) plus the activation, padded to 2 mod 4."""
+    nf = dim * dim + dim + 1 + (dim if spring else 0)
+    rs = nf + 1
+    while rs % 4 != 2:
+        rs += 1
+    return rs
+
+
+def build(L, p, te, tv=256, rs=None):
     X = np.ascontiguousarray(p.X, np.float64)
     T = np.ascontiguousarray(p.T, np.int32)
     fx = np.ascontiguousarray(p.fixed, np.uint8)
     err = C.create_string_buffer(256)
-    h = L.tb_build(p.dim, len(X), len(T), X.ctypes.data, T.ctypes.data, fx.ctypes.data, te, tv, err, 256)
+    rs = rec_stride(p.dim) if rs is None else rs
+    h = L.tb_build(p.dim, len(X), len(T), X.ctypes.data, T.ctypes.data, fx.ctypes.data, te, tv, rs, err, 256)
     if not h:
         raise ValueError(err.value.decode())
     out = {n: np.zeros(L.tb_len(h, i), DT[i]) for i, n in enumerate(NAMES)}
@@ -63,6 +75,7 @@ def build(L, p, te, tv=256):
             L.tb_copy(h, i, out[n].ctypes.data)
     for i, n in enumerate(["n_tiles", "max_te", "max_tv", "ne_int", "n_slots"]):
         out[n] = L.tb_scalar(h, i)
+    out["rs"] = rs
     L.tb_free(h)
     return out
 
@@ -111,13 +124,16 @@ def test_tile_layout_invariants(lib, name):
         lids = np.stack([(conn >> (8 * k)) & 0xFF for k in range(nc)], axis=1)
         assert np.array_equal(gid[lids], p.T[perm[:n_real]])
         assert set(g_real.tolist()) == set(p.T[perm[:n_real]].ravel().tolist())
-        # incidence lists: offsets corner*d*max_te + local elem, each corner exactly once
+        # incidence lists: offsets local elem*rs + corner*d, each corner exactly once
         lists = tile_lists(t, ti, nc)
         seen = np.zeros((n_real, nc), int)
+        rs = t["rs"]
         for k in np.nonzero(real_lv)[0]:
             offs = lists[k]
             assert len(offs) == count[k]
-            corner, le = offs // (d * max_te), offs % (d * max_te)
+            le, slot = offs // rs, offs % rs
+            assert (slot % d == 0).all() and (slot < nc * d).all()
+            corner = slot // d
             assert (le < n_real).all()
             assert (lids[le, corner] == k).all()
             seen[le, corner] += 1
@@ -166,8 +182,7 @@ def _corner_wavefronts(t, nc, element_order=False):
     for ti in range(t["n_tiles"]):
         lists = tile_lists(t, ti, nc)
         if element_order:
-            lists = [x[np.argsort(x % ((nc - 1) * t["max_te"]), kind="stable")]
-                     for x in lists]
+            lists = [np.sort(x) for x in lists]  # offsets grow with the local element
         for g0 in range(0, len(lists), 32):
             ks = range(g0, min(g0 + 32, len(lists)))
             for i in range(max(len(lists[k]) for k in ks)):
@@ -178,16 +193,16 @@ def _corner_wavefronts(t, nc, element_order=False):
 
 
 def test_incidence_lists_are_bank_aware(lib):
-    # a block of 6-tet hexes cut into tiles of 384 tets (the default 3D tile):
-    # the builder's order of each vertex's incidences spreads the lanes of a
-    # warp over the banks; listing them in element order instead conflicts
-    # about twice as often
+    # a block of 6-tet hexes cut into tiles of 384 tets (the default 3D tile,
+    # records of 14 words): the builder's order of each vertex's incidences
+    # spreads the lanes of a warp over the banks; listing them in element
+    # order instead conflicts about twice as often
     p = synth.make_small3d(16, 8, 8, split=6)
     t = build(lib, p, 384)
     nc = p.dim + 1
     ours = _corner_wavefronts(t, nc)
     base = _corner_wavefronts(t, nc, element_order=True)
-    assert ours <= 1.5 and base >= 1.5 * ours, (ours, base)
+    assert ours <= 1.75 and base >= 1.8 * ours, (ours, base)
 
 
 def _list_wavefronts(t, packed=False):

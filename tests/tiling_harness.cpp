@@ -11,11 +11,11 @@ using softsim::TileBuild;
 extern "C" {
 
 void *tb_build(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed, int te_max,
-               int tv_max, char *err, int err_len)
+               int tv_max, int rec_stride, char *err, int err_len)
 {
     TileBuild *tb = new (std::nothrow) TileBuild();
     std::string e;
-    if (!tb || !softsim::build_tiles(dim, nv, ne, X, T, fixed, te_max, tv_max, *tb, e)) {
+    if (!tb || !softsim::build_tiles(dim, nv, ne, X, T, fixed, te_max, tv_max, rec_stride, *tb, e)) {
         if (err && err_len > 0) {
             std::strncpy(err, e.c_str(), err_len - 1);
             err[err_len - 1] = 0;
