@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256) k_tile_grad(TileDev td, ElemDev<double> e
                 for (int k = 0; k < D; ++k) s += (mu * F[i][k] + cc * C[i][k]) * B[j][k];
                 G[i][j] = W * (s + ka * Ff[i] * gv[j]);
             }
-        store_corners<double, D>(scr + (int64_t)le * td.rs, G);
+        store_corners<double, D>(scr + (int64_t)le * td.rs + corner_base(le), G);
     }
     __syncthreads();
     double gn2 = 0.0;
@@ -422,7 +422,8 @@ struct HvpSmem {
 // tables into shared memory with bulk copies on two mbarriers; the tile's
 // vertex values are then gathered, each thread evaluates dP(dF) for its
 // elements from their records (pair loads), the element's corner forces
-// overwrite its own record in place ((D+1)*D <= RS slots), and one thread
+// overwrite its own record in place (slots corner_base(le) .. +(D+1)*D <= RS),
+// and one thread
 // per local vertex adds its corners in fixed order.
 // SPRING selects the active-spring muscle at compile time, so the
 // contractile kernel carries none of its code or its extra fields.
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
 #pragma unroll
                 for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
         }
-        store_corners<T, D>(sRec + le * RS, G);  // overwrites this element's own record only
+        store_corners<T, D>(sRec + le * RS + corner_base(le), G);  // overwrites this element's own record only
     }
     __syncthreads();
     // p.Ap of this thread in the kernel's precision: in the mixed kernel the

@@ -48,7 +48,7 @@ struct TileDev {
     const int32_t *lv_code = nullptr;    // [n_lv]
     const uint32_t *lv_inc = nullptr;    // [n_lv] first incidence (within the tile) | count << 16 | pinned
     // inc entries: the offset of a corner's dim values among the tile's element
-    // records, local element * rs + corner * dim
+    // records, local element * rs + corner_base(local element) + corner * dim
     const uint16_t *inc = nullptr;       // [ne_int * (dim+1)]
     const uint32_t *conn = nullptr;      // [ne_int]
     const int32_t *perm = nullptr;       // [ne_int] tile order -> caller order, -1 = padding

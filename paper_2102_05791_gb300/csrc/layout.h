@@ -26,6 +26,12 @@ constexpr uint32_t kLvCountMask = 0x7fffu;
 #endif
 SOFTSIM_HD constexpr int hvp_fields(int dim, bool spring) { return dim * dim + dim + 1 + (spring ? dim : 0); }
 SOFTSIM_HD constexpr int rec_stride(int nf) { return nf + 1 + ((2 - (nf + 1) % 4) + 4) % 4; }
+// First slot of the corner forces in the record of local element le: 0 or 2.
+// With an even stride, records le and le + 16 start in the same bank; moving
+// the corner block of half the elements by two words (pair-aligned) spreads
+// the vertex phase's corner loads over more banks (bit 6 measured best on
+// the tiles of a 6-tet hex mesh; any bit from 4 up does about as well).
+SOFTSIM_HD constexpr int corner_base(int le) { return 2 * ((le >> 6) & 1); }
 #undef SOFTSIM_HD
 
 }  // namespace softsim

@@ -124,7 +124,7 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
     out.ne = ne;
     if (tv_max > 256) tv_max = 256;
     if (te_max < 1) te_max = 1;
-    if (rec_stride < nc * dim) {
+    if (rec_stride < nc * dim + 2) {
         err = "element record stride too small for the corner forces";
         return false;
     }
@@ -243,7 +243,8 @@ bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t
         for (int i = es; i < es + n_real; ++i)
             for (int k = 0; k < nc; ++k) {
                 const int l = loc[T[(int64_t)out.perm[i] * nc + k]];
-                out.inc[base + fill[l]++] = (uint16_t)((i - es) * rec_stride + k * dim);
+                out.inc[base + fill[l]++] =
+                    (uint16_t)((i - es) * rec_stride + corner_base(i - es) + k * dim);
             }
         bank_order(out.inc.data() + base, bucket, nl);
         const std::vector<int32_t> first = bank_place(out.inc.data() + base, bucket, nl);

@@ -29,7 +29,7 @@ struct TileBuild {
     std::vector<int32_t> tile_vert;  // [n_tiles + 1] padded local-vertex offsets
     std::vector<int32_t> lv_gid, lv_code;
     std::vector<uint32_t> lv_inc;    // first incidence | count << 16 | kLvPinned
-    std::vector<uint16_t> inc;       // [ne_int * (dim+1)] corner offsets local elem*rs + corner*dim
+    std::vector<uint16_t> inc;       // [ne_int * (dim+1)] corner offsets le*rs + corner_base(le) + corner*dim
     std::vector<uint32_t> conn;      // [ne_int]
     std::vector<int32_t> fin_gid, fin_ptr;
     std::vector<int32_t> vfin;       // [nv] index into fin_gid, or -1 for a vertex of one tile
@@ -39,8 +39,8 @@ struct TileBuild {
 // mean element size) and cuts the order greedily into tiles of at most
 // te_max elements and at most tv_max (<= 256) distinct vertices.  `T` is
 // [ne][dim+1] in caller order; rec_stride is the stride (in words) of the
-// per-element records whose slots corner*dim .. corner*dim+dim-1 hold the
-// corner forces in the kernels.  Returns false and sets err if some vertex
+// per-element records whose slots corner_base(le) + corner*dim .. + dim-1
+// hold the corner forces in the kernels.  Returns false and sets err if some vertex
 // belongs to no element or a single element exceeds the limits.
 bool build_tiles(int dim, int64_t nv, int64_t ne, const double *X, const int32_t *T, const uint8_t *fixed,
                  int te_max, int tv_max, int rec_stride, TileBuild &out, std::string &err);

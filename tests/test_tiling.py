@@ -132,7 +132,8 @@ def test_tile_layout_invariants(lib, name):
             offs = lists[k]
             assert len(offs) == count[k]
             le, slot = offs // rs, offs % rs
-            assert (slot % d == 0).all() and (slot < nc * d).all()
+            slot = slot - 2 * ((le >> 6) & 1)  # corner block moved by two words in half the records
+            assert (slot >= 0).all() and (slot % d == 0).all() and (slot < nc * d).all()
             corner = slot // d
             assert (le < n_real).all()
             assert (lids[le, corner] == k).all()
@@ -202,7 +203,7 @@ def test_incidence_lists_are_bank_aware(lib):
     nc = p.dim + 1
     ours = _corner_wavefronts(t, nc)
     base = _corner_wavefronts(t, nc, element_order=True)
-    assert ours <= 1.75 and base >= 1.8 * ours, (ours, base)
+    assert ours <= 1.6 and base >= 1.8 * ours, (ours, base)
 
 
 def _list_wavefronts(t, packed=False):
