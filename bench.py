@@ -471,7 +471,9 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": "elem-HVP/s",
                 "h2d_bytes_per_step": int(X_host.numel() * 8 + a_host.numel() * 8),
-                "d2h_bytes_per_step": int(out_g.numel() * 8 + out_x.numel() * 8)},
+                "d2h_bytes_per_step": int(out_g.numel() * 8 + out_x.numel() * 8),
+                # its own solves: the Newton path (and so the HVP count) depends on rounding order
+                "hvp_per_step": e2e_all / max(args.steps, 1)},
         "roofline": roof,
         "clocks": clk,
     }
