@@ -398,6 +398,141 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
 
 // ---------------------------------------------------------------- HVP
 
+// One element of the HVP: reads the element's record (pair loads) and the
+// staged u and v of its vertices, evaluates G = W dP(dF) Dm^-T plus the
+// muscle term, adds v_e . (H_e v_e) to qsum (CG), and overwrites the record
+// in place with the element's corner forces.
+template <typename T, int D, bool CG, bool SPRING, int RS>
+__device__ __forceinline__ void hvp_element(T *rec, int le, uint32_t cword, const T *suv, const Phys &ph, T mu,
+                                            T lam, T sel, T kk, T &qsum)
+{
+    constexpr int NF = hvp_fields(D, SPRING);
+    int lid[D + 1];
+    unpack<D>(cword, lid);
+    // Dm^-1, g and W first (for the contractile muscle that includes the
+    // activation); the spring's fiber and activation where they are used
+    constexpr int N1 = (FI<D>::W + 2) / 2 * 2;
+    T rv[RS];
+    load_pairs<T, N1>(rec, rv);
+    T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D], gv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) B[i][j] = rv[FI<D>::B + i * D + j];
+#pragma unroll
+    for (int i = 0; i < D; ++i) gv[i] = rv[FI<D>::G + i];
+    const T W = rv[FI<D>::W] * sel;
+    edges_uv<T, D>(suv, lid, Du, Dv);
+    mul<T, D>(Du, B, F, true);
+    mul<T, D>(Dv, B, dF, false);
+    cof<T, D>(F, C);
+    dcof<T, D>(F, dF, dC);
+    const T J = detF<T, D>(F, C);
+    T dJ = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) dJ += C[i][j] * dF[i][j];
+    T l, cc, cp;
+    log_terms<T>(ph.log_mode, mu, lam, J, l, cc, cp);
+    const T cpdJ = cp * dJ;
+    T dvg[D];  // (d2psi_m/dq2) dq with dq = dF f = Dv g
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
+        dvg[i] = s;
+    }
+    if constexpr (N1 < RS) load_pairs<T, RS - N1>(rec + N1, rv + N1);
+    const T aval = rv[NF];
+    if constexpr (SPRING) {  // spring, with q = F f = f + Du g
+        T q[D], s2 = T(0), qdq = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            T s = rv[FI<D>::F + i];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
+            q[i] = s;
+            s2 += s * s;
+            qdq += s * dvg[i];
+        }
+        T c1, c2;
+        spring_terms<T>(W != T(0), kk, aval, sqrt(s2), c1, c2);
+#pragma unroll
+        for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dvg[i] *= kk * aval;
+    }
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
+            G[i][j] = W * (s + dvg[i] * gv[j]);
+        }
+    if (CG) {
+        // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
+    }
+    store_corners<T, D>(rec + corner_base(le), G);  // overwrites this element's own record only
+}
+
+// One local vertex of the HVP: adds its corners in fixed order, adds the
+// per-vertex terms (contact curvature, inertia, friction) where it owns
+// them, and writes A v (single-tile vertex, masked) or its halo partial; the
+// owner's vertex terms of p.Ap go to dot (CG).  uv: the vertex's staged
+// record [u (D), v (D)].
+template <typename T, int D, bool CG>
+__device__ __forceinline__ void hvp_vertex(int code, uint32_t linc, int64_t gid, const T *uv, const uint16_t *sInc,
+                                           const T *sRec, const VertDev &vd, const Phys &ph, T *__restrict__ y,
+                                           T *__restrict__ hp, T &dot)
+{
+    if (code == LV_PAD) return;
+    T acc[D];
+    gather_corners<T, D>(sInc, linc, sRec, acc);
+    const bool contact = ph.contact != 0, dyn = ph.dyn != 0;
+    const bool interior = code == LV_INTERIOR;
+    const bool owner = CG && (interior || (code & 1));  // counts the vertex terms of p.Ap
+    if ((interior || owner) && (contact || dyn)) {
+        T kcv = T(0), m = T(0), mh = T(0);  // contact curvature and inertia (+ friction) diagonals
+        if (contact) {
+            const double yy = vd.X[gid * D + 1] + (double)uv[1];
+            const double pen = yy < 0.0 ? -yy : 0.0;
+            const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
+            kcv = T(ph.s_el * d2);
+        }
+        if (dyn) {
+            m = T(vd.mass[gid]);
+            mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
+        }
+        T dv[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * uv[D + c];
+        if (interior)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += dv[c];
+        if (owner)
+#pragma unroll
+            for (int c = 0; c < D; ++c) dot += dv[c] * uv[D + c];
+    }
+    if (interior) {
+        const bool fx = (linc & kLvPinned) != 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
+    }
+}
+
 // Shared-memory plan of the HVP tile kernel (offsets in bytes, all 16-byte
 // aligned because max_te is a multiple of 8, max_tv of 4 and rs even).
 template <typename T, int D>
@@ -504,129 +639,15 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     const T mu = pick<T>(ph.mu, ph.mu_f), lam = pick<T>(ph.lam, ph.lam_f);
     const T sel = pick<T>(ph.s_el, ph.s_el_f), kk = pick<T>(ph.k, ph.k_f);
     T qsum = T(0);  // CG: sum of the element quadratic forms v_e . (H_e v_e) of this thread
-    for (int le = threadIdx.x; le < ne_t; le += blockDim.x) {
-        int lid[D + 1];
-        unpack<D>(sConn[le], lid);
-        // Dm^-1, g and W first (for the contractile muscle that includes the
-        // activation); the spring's fiber and activation where they are used
-        constexpr int N1 = (FI<D>::W + 2) / 2 * 2;
-        T rv[RS];
-        load_pairs<T, N1>(sRec + le * RS, rv);
-        T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D], gv[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) B[i][j] = rv[FI<D>::B + i * D + j];
-#pragma unroll
-        for (int i = 0; i < D; ++i) gv[i] = rv[FI<D>::G + i];
-        const T W = rv[FI<D>::W] * sel;
-        edges_uv<T, D>(suv, lid, Du, Dv);
-        mul<T, D>(Du, B, F, true);
-        mul<T, D>(Dv, B, dF, false);
-        cof<T, D>(F, C);
-        dcof<T, D>(F, dF, dC);
-        const T J = detF<T, D>(F, C);
-        T dJ = T(0);
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) dJ += C[i][j] * dF[i][j];
-        T l, cc, cp;
-        log_terms<T>(ph.log_mode, mu, lam, J, l, cc, cp);
-        const T cpdJ = cp * dJ;
-        T dvg[D];  // (d2psi_m/dq2) dq with dq = dF f = Dv g
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            T s = T(0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
-            dvg[i] = s;
-        }
-        if constexpr (N1 < RS) load_pairs<T, RS - N1>(sRec + le * RS + N1, rv + N1);
-        const T aval = rv[NF];
-        if constexpr (SPRING) {  // spring, with q = F f = f + Du g
-            T q[D], s2 = T(0), qdq = T(0);
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                T s = rv[FI<D>::F + i];
-#pragma unroll
-                for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
-                q[i] = s;
-                s2 += s * s;
-                qdq += s * dvg[i];
-            }
-            T c1, c2;
-            spring_terms<T>(W != T(0), kk, aval, sqrt(s2), c1, c2);
-#pragma unroll
-            for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
-        } else {
-#pragma unroll
-            for (int i = 0; i < D; ++i) dvg[i] *= kk * aval;
-        }
-        T G[D][D];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                T s = T(0);
-#pragma unroll
-                for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
-                G[i][j] = W * (s + dvg[i] * gv[j]);
-            }
-        if (CG) {
-            // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
-        }
-        store_corners<T, D>(sRec + le * RS + corner_base(le), G);  // overwrites this element's own record only
-    }
+    for (int le = threadIdx.x; le < ne_t; le += blockDim.x)
+        hvp_element<T, D, CG, SPRING, RS>(sRec + le * RS, le, sConn[le], suv, ph, mu, lam, sel, kk, qsum);
     __syncthreads();
     // p.Ap of this thread in the kernel's precision: in the mixed kernel the
     // block sum stays FP32 too (GB300's FP64 pipe runs at 1/64 of FP32) and
     // the tile partials are summed with compensation by k_cg_alpha.
     T dot = qsum;
-    const bool contact = ph.contact != 0, dyn = ph.dyn != 0;
-    for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
-        const int code = sCode[k];
-        if (code == LV_PAD) continue;
-        T acc[D];
-        gather_corners<T, D>(sInc, sLinc[k], sRec, acc);
-        const int64_t gid = sGid[k];
-        const bool interior = code == LV_INTERIOR;
-        const bool owner = CG && (interior || (code & 1));  // counts the vertex terms of p.Ap
-        if ((interior || owner) && (contact || dyn)) {
-            T kcv = T(0), m = T(0), mh = T(0);  // contact curvature and inertia (+ friction) diagonals
-            if (contact) {
-                const double yy = vd.X[gid * D + 1] + (double)suv[k * 2 * D + 1];
-                const double pen = yy < 0.0 ? -yy : 0.0;
-                const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-                kcv = T(ph.s_el * d2);
-            }
-            if (dyn) {
-                m = T(vd.mass[gid]);
-                mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
-            }
-            T dv[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * suv[k * 2 * D + D + c];
-            if (interior)
-#pragma unroll
-                for (int c = 0; c < D; ++c) acc[c] += dv[c];
-            if (owner)
-#pragma unroll
-                for (int c = 0; c < D; ++c) dot += dv[c] * suv[k * 2 * D + D + c];
-        }
-        if (interior) {
-            const bool fx = (sLinc[k] & kLvPinned) != 0;
-#pragma unroll
-            for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
-        } else {
-#pragma unroll
-            for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
-        }
-    }
+    for (int k = threadIdx.x; k < nlv; k += blockDim.x)
+        hvp_vertex<T, D, CG>(sCode[k], sLinc[k], sGid[k], suv + k * 2 * D, sInc, sRec, vd, ph, y, hp, dot);
     pdl_trigger();  // the alpha reduction may be scheduled once every tile is done
     if (CG) {
         const T sum = block_sum(dot);

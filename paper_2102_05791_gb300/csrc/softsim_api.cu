@@ -425,7 +425,7 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     CK(h, cudaEventCreate(&h->ev1));
     CK(h, configure_elem_kernels());
     const size_t sm_need = is_mixed(h) ? hvp_smem<float>(c) : hvp_smem<double>(c);
-    const size_t sm_grad = (size_t)td.max_tv * d * sizeof(double) + (size_t)td.max_te * nc * d * sizeof(double);
+    const size_t sm_grad = (size_t)td.max_tv * d * sizeof(double) + (size_t)td.max_te * td.rs * sizeof(double);
     if (std::max(sm_need, sm_grad) > 200 * 1024) return fail(h, SIM_EINVAL, "tile too large for shared memory");
     CK(h, cudaDeviceSynchronize());
     return SIM_OK;
