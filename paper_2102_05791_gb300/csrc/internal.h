@@ -6,7 +6,12 @@
 //     max_tv (<= 256) vertices.  perm[e] maps tile order -> caller order.
 //   * Per-element static data is structure-of-arrays, one field per array of
 //     `stride` entries: Dm^-1 (dim*dim fields, row-major), g = Dm^-1 f (dim),
-//     W (1), f (dim).  The HVP reads only the first dim*dim + dim + 1 fields.
+//     W (1), f (dim); FP64, read by the energy, gradient and VJP kernels.
+//   * The HVP kernels read per-element records instead, [ne_int][rs] (FP32 and
+//     FP64 copies): the hvp_fields() fields in the order above (f only with
+//     the spring muscle), the activation, padding to rs = rec_stride(), and
+//     in shared memory the element's corner forces overwrite its own record
+//     from slot corner_base(local elem).
 //   * conn[e] packs the element's dim+1 tile-local vertex ids, 8 bits each.
 //   * A tile's local vertices are lv_gid[tile_vert[t] .. tile_vert[t+1]),
 //     sorted by global id.  lv_code < 0: the vertex belongs to this tile only
@@ -18,9 +23,11 @@
 //     every vertex sum is formed in one fixed order (deterministic, no float
 //     atomics).
 //   * inc[tile_elem[t]*(dim+1) + s], s in [first, first+count) of lv_inc[lv],
-//     lists the corners that touch local vertex lv, in order of increasing
-//     local element, each encoded as its offset corner*dim*max_te +
-//     local_elem in the corner buffer; lv_inc also flags pinned vertices.
+//     lists the corners that touch local vertex lv, each encoded as the
+//     offset local_elem*rs + corner_base(local_elem) + corner*dim of its dim
+//     values among the tile's records; the tile builder picks the order of
+//     each list and where it starts so that the lanes of a warp read from
+//     distinct shared-memory banks.  lv_inc also flags pinned vertices.
 //   * Per-tile ranges are padded to 16-byte multiples for bulk copies;
 //     padding elements have W = 0 and perm -1, padding local vertices have
 //     lv_code == LV_PAD and no incidences.
