@@ -33,6 +33,9 @@ def lib(tmp_path_factory):
     L.tb_len.argtypes = [vp, C.c_int]
     L.tb_len.restype = C.c_int64
     L.tb_copy.argtypes = [vp, C.c_int, vp]
+    for f, n in (("tb_hvp_fields", 2), ("tb_rec_stride", 1), ("tb_corner_base", 1)):
+        getattr(L, f).argtypes = [C.c_int] * n
+        getattr(L, f).restype = C.c_int
     return L
 
 
@@ -243,6 +246,25 @@ def test_incidence_lists_are_placed_bank_aware(lib):
         for f, c in zip(first, count):
             cover[f:f + c] += 1
         assert (cover == 1).all()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("spring", [0, 1])
+def test_element_record_layout(lib, dim, spring):
+    # the HVP record: the element fields (Dm^-1, g, W; f with the spring), the
+    # activation, padding to a stride of 2 mod 4 words (conflict-free pair
+    # loads across a warp); the corner block fits after its base in every
+    # record and starts pair-aligned
+    nf = lib.tb_hvp_fields(dim, spring)
+    assert nf == dim * dim + dim + 1 + (dim if spring else 0)
+    rs = lib.tb_rec_stride(nf)
+    assert rs == rec_stride(dim, bool(spring)) and rs >= nf + 1 and rs % 4 == 2 and rs < nf + 5
+    for le in range(1024):
+        base = lib.tb_corner_base(le)
+        assert base % 2 == 0 and base + (dim + 1) * dim <= rs
+    # pair loads of 32 consecutive records hit 16 distinct 8-byte bank pairs per half warp
+    pairs = [(rs * le // 2) % 16 for le in range(16)]
+    assert len(set(pairs)) == 16
 
 
 def test_single_tile_has_no_halo(lib):

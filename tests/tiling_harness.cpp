@@ -79,4 +79,9 @@ void tb_copy(void *h, int which, void *dst)
     case 10: std::memcpy(dst, t->vfin.data(), t->vfin.size() * 4); break;
     }
 }
+
+// The element-record layout constants shared by the builder and the kernels.
+int tb_hvp_fields(int dim, int spring) { return softsim::hvp_fields(dim, spring != 0); }
+int tb_rec_stride(int nf) { return softsim::rec_stride(nf); }
+int tb_corner_base(int le) { return softsim::corner_base(le); }
 }
