@@ -31,8 +31,8 @@ static uint64_t spread2(uint64_t x)
 
 // Orders each local vertex's incidence list for the vertex phase of the tile
 // kernels, where lane j of a warp walks the list of local vertex 32w + j:
-// at every step the lanes read corner entries of the corner buffer, whose
-// shared-memory bank is the entry's word offset mod 32.  Greedily, step by
+// at every step the lanes read corner forces from the tile's element records
+// in shared memory, whose bank is the entry's word offset mod 32.  Greedily, step by
 // step, each lane takes the remaining entry whose bank the other lanes of the
 // step have used least (lanes with the fewest entries left choose first;
 // ties go to the lower offset), so the lanes of a step mostly hit distinct
