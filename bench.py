@@ -203,12 +203,16 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("elem_kernels.cu", "tiling.cpp", "elem_math.cuh", "layout.h", "tma.cuh", "reduce.cuh", "pdl.cuh",
+                  "internal.h")
+
+
 def kernel_source_hash():
-    """Hash of the element-kernel source and of the tile builder (which lays
-    out the kernel's inputs), without their // comment lines: counters taken
-    on the same code stay valid across comment edits."""
+    """Hash of the element-kernel source, the headers it includes and the tile
+    builder (which lays out the kernel's inputs), without their // comment
+    lines: counters taken on the same code stay valid across comment edits."""
     lines = []
-    for f in ("elem_kernels.cu", "tiling.cpp"):
+    for f in KERNEL_SOURCES:
         src = os.path.join(ROOT, "paper_2102_05791_gb300", "csrc", f)
         lines += [ln for ln in open(src).read().splitlines() if not ln.strip().startswith("//")]
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
