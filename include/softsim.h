@@ -257,6 +257,15 @@ int sim_time_hvp(sim_handle *h, int n_launches, float *ms, void *stream);
 int sim_set_kernel_timing(sim_handle *h, int on);
 int sim_kernel_timing(const sim_handle *h, double *hvp_tile_ms, int64_t *hvp_launches);
 
+/* Poll limit of the first bulk-copy wait in the HVP tile kernels (the wait
+ * for a tile's vertex tables), for testing the timeout path: polls >= 0 sets
+ * it (0 = give up at once), polls < 0 restores the library default (the
+ * bound of every other wait).  A kernel whose wait runs out raises a flag,
+ * lets the copies it issued land, and exits without touching the unfinished
+ * data; the solver call that launched it then returns SIM_ECUDA ("gave up
+ * waiting") and clears the flag, so the handle's next call starts clean. */
+int sim_set_wait_limit(sim_handle *h, int polls);
+
 /* Number of CUDA kernels the handle has launched so far (graph replays count
  * every kernel node they run). */
 int sim_counters(const sim_handle *h, int64_t *kernel_launches);
@@ -316,13 +325,17 @@ int sim_batch_rollout(sim_batch *b, int n_steps, double *states_x, double *state
  * ignored).  It needs no handle and allocates no device memory, for callers
  * that cannot call cudaMalloc at that point: a process whose GPU memory is
  * already claimed by another framework's pool allocator, or code that must
- * not allocate after its setup.  Its scratch (block partial sums and a
- * counter, about 33 KB) is a fixed array inside the library that every GPU
+ * not allocate after its setup.  Its scratch (block partial sums and two
+ * counters, about 33 KB) is a fixed array inside the library that every GPU
  * loading the library keeps until exit.  At most 4,194,304 elements and
  * vertices; larger meshes get SIM_EINVAL.  The first call on a device looks
  * up the array's address (with that device current) and must come before
  * any stream capture.  Calls share the array, so calls that overlap on the
- * GPU race; serialise them.  Errors: sim_noalloc_last_error(). */
+ * GPU race; serialise them.  The call waits for `stream` before it returns:
+ * a rest element with non-positive area or volume (which sim_create would
+ * reject) gives SIM_EINVERTED, with E_out = NaN.  Under SIM_LOG_EXACT a
+ * state with some J <= 0 gives E = +inf and SIM_OK, as in sim_energy_grad.
+ * Errors: sim_noalloc_last_error(). */
 int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const double *rest_pos,
                        const int32_t *elems, const double *x, const double *a, const double *fiber,
                        const sim_material *mat, double *E_out, void *stream);

@@ -25,7 +25,7 @@ EXPORTED = [
     "sim_energy_grad", "sim_hvp", "sim_newton_solve", "sim_adjoint_solve", "sim_param_vjp", "sim_material_vjp",
     "sim_step_forward", "sim_step_backward", "sim_rollout", "sim_rollout_backward",
     "sim_time_hvp", "sim_tile_stats", "sim_counters", "sim_energy_noalloc", "sim_noalloc_last_error",
-    "sim_set_kernel_timing", "sim_kernel_timing",
+    "sim_set_kernel_timing", "sim_kernel_timing", "sim_set_wait_limit",
     "sim_batch_create", "sim_batch_destroy", "sim_batch_last_error", "sim_batch_sizes", "sim_batch_rollout",
 ]
 
@@ -93,6 +93,7 @@ def load(path: str | None = None):
     L.sim_counters.argtypes = [H, C.POINTER(C.c_int64)]
     L.sim_set_kernel_timing.argtypes = [H, i]
     L.sim_kernel_timing.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.sim_set_wait_limit.argtypes = [H, i]
     L.sim_energy_noalloc.argtypes = [i, C.c_int64, C.c_int64, vp, vp, vp, vp, vp, C.POINTER(SimMaterial), vp, vp]
     L.sim_noalloc_last_error.argtypes = []
     L.sim_noalloc_last_error.restype = C.c_char_p

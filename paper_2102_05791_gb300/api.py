@@ -244,6 +244,11 @@ class Simulator:
         self._lib.sim_kernel_timing(self._h, C.byref(ms), C.byref(n))
         return float(ms.value), int(n.value)
 
+    def set_wait_limit(self, polls):
+        """Poll limit of the HVP tile kernel's first bulk-copy wait (testing aid;
+        negative restores the default)."""
+        self._check("sim_set_wait_limit", self._lib.sim_set_wait_limit(self._h, int(polls)))
+
     def kernel_launches(self):
         n = C.c_int64()
         self._lib.sim_counters(self._h, C.byref(n))

@@ -1,7 +1,7 @@
 """Build libsoftsim.so in-tree with nvcc for sm_103a (no CMake, no torch).
 
-The four translation units are compiled in parallel, then linked into
-paper_2102_05791_gb300/libsoftsim.so next to this file.  Rebuilds only what
+The translation units listed in SOURCES are compiled in parallel, then
+linked into paper_2102_05791_gb300/libsoftsim.so next to this file.  Rebuilds only what
 changed (by modification time).
 """
 from __future__ import annotations

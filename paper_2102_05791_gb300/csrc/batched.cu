@@ -323,7 +323,7 @@ __device__ double energy_pass(const BatchDev &b, const Mesh &m, const double *a_
             l = (J - 1.0) - 0.5 * (J - 1.0) * (J - 1.0);
         double w = s_el * W *
                    (0.5 * m.mu * (I1 - D) - m.mu * l + 0.5 * m.lam * l * l + muscle_psi(b, a_t[e], Ff2));
-        if (b.log_mode == 0 && !(J > 0.0)) w = INFINITY;
+        if (b.log_mode == 0 && J <= 0.0) w = INFINITY;  // a NaN J (non-finite input) stays NaN
         E += w;
         A += fabs(w);
     }
@@ -645,7 +645,7 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
     double rn = bn;
     int status = SIM_ENOTCONVERGED;
     int budget = b.max_adj_cg;
-    for (int pass = 0; pass < 12; ++pass) {
+    for (int pass = 0; pass < 12 && isfinite(bn); ++pass) {
         if (rn <= b.adj_rtol * bn || !(rn > 0.0)) {
             status = SIM_OK;
             break;
@@ -676,6 +676,7 @@ __device__ int step_backward(const BatchDev &b, const Mesh &m, const double *x0,
         rn = rnew;
     }
     if (rn <= b.adj_rtol * bn) status = SIM_OK;
+    if (!isfinite(bn)) status = SIM_ENAN;  // non-finite right-hand side
     // xbar0 = M lambda - vbar1/h, vbar0 = h M lambda; with friction, plus
     // fw lambda_h on the horizontal axes and 2 k_f [y0 < eps] lambda_h . (x1 - x0)_h on y
     for (int lv = threadIdx.x; lv < m.nv; lv += blockDim.x) {

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_tile_energy(TileDev td, ElemDev<double>
                 musc = W != 0.0 ? 0.5 * ph.k * r * r : 0.0;
             }
             double w = ph.s_el * W * (0.5 * mu * (I1 - D) - mu * l + 0.5 * lam * l * l + musc);
-            if (ph.log_mode == 0 && !(J > 0.0)) w = INFINITY;
+            if (ph.log_mode == 0 && J <= 0.0) w = INFINITY;  // a NaN J (non-finite input) stays NaN
             Eacc[j] += w;
             Sacc[j] += fabs(w);
         }
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
         return;
     }
     // every thread takes the same decision, so no thread is left at a barrier
-    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0, td.wait_polls))) {
         if (threadIdx.x == 0) {
             atomicOr(&sc->kerr, 1);
             mbar_wait_bounded(bar, 0);  // give copies in flight a last chance before the CTA exits

@@ -62,6 +62,10 @@ struct TileDev {
     const int32_t *fin_gid = nullptr;    // [n_fin]
     const int32_t *fin_ptr = nullptr;    // [n_fin + 1]
     const int32_t *vfin = nullptr;       // [nv] halo index of a vertex, -1 if one tile owns it
+    // poll limit of the HVP tile kernel's first bulk-copy wait (the copies of
+    // the vertex tables); the library default is the same bound as every
+    // other wait, and sim_set_wait_limit lowers it to exercise the error path
+    int wait_polls = 1 << 22;
 };
 
 template <typename T>

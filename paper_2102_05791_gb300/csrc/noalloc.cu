@@ -6,8 +6,9 @@
 // process whose GPU memory has been claimed up front by another framework's
 // pool allocator, or code that must not allocate once its setup is done.
 // This entry point needs no handle (building a handle allocates) and keeps
-// its only scratch -- one FP64 partial sum per block plus the block counter
-// of the final reduction -- in a fixed-size array that lives in the library
+// its only scratch -- one FP64 partial sum per block, the block counter of
+// the final reduction and a count of invalid rest elements -- in a fixed-size
+// array that lives in the library
 // image.  Every GPU that loads the library holds that array (about 33 KB)
 // until the process exits.
 //
@@ -16,6 +17,9 @@
 // first call before capturing a stream.  All calls share the array and it
 // keeps the last call's contents, so calls that overlap on the GPU (on
 // different streams, or from different host threads) race; serialise them.
+// A rest element with non-positive area or volume makes the mesh invalid:
+// the call then waits for its stream, finds the element count the kernel
+// recorded, and returns SIM_EINVERTED (E_out holds NaN).
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -33,7 +37,8 @@ constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
     double partial[kNoAllocBlocks];
-    unsigned int ticket;
+    unsigned int ticket;      // blocks done (last-block reduction)
+    unsigned int n_inverted;  // rest elements with non-positive measure
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -41,6 +46,7 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 std::mutex g_setup_mutex;
 NoAllocScratch *g_scratch_ptr[kMaxDevices] = {nullptr};
 thread_local std::string g_noalloc_error;
+thread_local unsigned int g_inverted_host;  // read-back target of the inverted-element count
 
 struct NoAllocMaterial {
     double mu, lam, k, rho, grav, kc;
@@ -52,7 +58,7 @@ struct NoAllocMaterial {
 // plus the element's share of the gravity potential, rho W g / (dim+1) * sum y.
 template <int D>
 __device__ double element_energy(int64_t e, const double *X, const int32_t *T, const double *x, const double *a,
-                                 const double *fiber, const NoAllocMaterial &m)
+                                 const double *fiber, const NoAllocMaterial &m, unsigned int *n_inverted)
 {
     const int32_t *t = T + e * (D + 1);
     double Dm[D][D], Ds[D][D];
@@ -80,7 +86,10 @@ __device__ double element_energy(int64_t e, const double *X, const int32_t *T, c
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) Bi[i][j] = C[j][i] / det;
     }
-    if (!(det > 0.0)) return NAN;  // inverted rest element: the mesh is invalid
+    if (!(det > 0.0)) {  // inverted rest element: the mesh is invalid
+        atomicAdd(n_inverted, 1u);
+        return NAN;
+    }
     const double W = det / (D == 2 ? 2.0 : 6.0);
     double F[D][D];
     for (int i = 0; i < D; ++i)
@@ -106,7 +115,7 @@ __device__ double element_energy(int64_t e, const double *X, const int32_t *T, c
     }
     double l;
     if (m.log_mode == SIM_LOG_EXACT) {
-        if (!(J > 0.0)) return INFINITY;
+        if (J <= 0.0) return INFINITY;  // a NaN J (non-finite input) stays NaN
         l = log(J);
     } else {
         l = (J - 1.0) - 0.5 * (J - 1.0) * (J - 1.0);
@@ -131,7 +140,7 @@ __global__ void __launch_bounds__(kNoAllocThreads)
     double s = 0.0;
     const int64_t b0 = (int64_t)blockIdx.x * kNoAllocPerBlock;
     for (int64_t e = b0 + threadIdx.x; e < ne && e < b0 + kNoAllocPerBlock; e += blockDim.x)
-        s += element_energy<D>(e, X, T, x, a, fiber, m);
+        s += element_energy<D>(e, X, T, x, a, fiber, m, &scratch->n_inverted);
     for (int64_t i = b0 + threadIdx.x; i < nv && i < b0 + kNoAllocPerBlock; i += blockDim.x) {
         const double y = x[i * D + 1];
         const double pen = y < 0.0 ? -y : 0.0;
@@ -195,8 +204,9 @@ extern "C" int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const
     int rc = scratch_for_current_device(&scratch);
     if (rc != SIM_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the block counter must start at zero; the partial sums are all overwritten
-    cudaError_t e = cudaMemsetAsync(&scratch->ticket, 0, sizeof(unsigned int), s);
+    // the block counter and the inverted-element count must start at zero;
+    // the partial sums are all overwritten
+    cudaError_t e = cudaMemsetAsync(&scratch->ticket, 0, 2 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return noalloc_fail(SIM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const NoAllocMaterial m{mat->mu, mat->lambda, mat->k_muscle, mat->density, mat->gravity, mat->k_contact,
                             mat->contact_power, mat->log_mode, mat->muscle_model};
@@ -210,5 +220,13 @@ extern "C" int sim_energy_noalloc(int dim, int64_t n_vert, int64_t n_elem, const
                                                              E_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(SIM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    // the status depends on the rest mesh: read the kernel's count (pageable
+    // host target, no allocation) and wait for the stream
+    e = cudaMemcpyAsync(&g_inverted_host, &scratch->n_inverted, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return noalloc_fail(SIM_ECUDA, std::string("read-back: ") + cudaGetErrorString(e));
+    if (g_inverted_host != 0)
+        return noalloc_fail(SIM_EINVERTED, std::to_string(g_inverted_host) +
+                                               " rest element(s) with non-positive area or volume; E is NaN");
     return SIM_OK;
 }

@@ -134,8 +134,23 @@ static int read_scalars(sim_handle *h, cudaStream_t s)
 {
     CK(h, cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
-    if (h->sc_host->kerr) return fail(h, SIM_ECUDA, "a kernel gave up waiting for its bulk copies");
+    if (h->sc_host->kerr) {
+        // clear the flag so that the handle's next call starts clean
+        CK(h, cudaMemsetAsync(&h->sc->kerr, 0, sizeof(int), s));
+        CK(h, cudaStreamSynchronize(s));
+        return fail(h, SIM_ECUDA, "a kernel gave up waiting for its bulk copies");
+    }
     return SIM_OK;
+}
+
+static void drop_graphs(sim_handle *h)
+{
+    for (auto &row : h->cg_graph)
+        for (auto &gr : row) {
+            if (gr.exec) cudaGraphExecDestroy(gr.exec);
+            gr.exec = nullptr;
+            gr.valid = false;
+        }
 }
 
 static bool is_mixed(const sim_handle *h) { return h->precision == SIM_PREC_MIXED; }
@@ -709,6 +724,13 @@ static int adjoint_impl(sim_handle *h, bool dyn, const double *b, double *lambda
     S.res0 = bn;
     S.min_J = NAN;
     S.status = SIM_ENOTCONVERGED;
+    if (!std::isfinite(bn)) {  // non-finite right-hand side: nothing to solve
+        S.status = SIM_ENAN;
+        S.res_final = bn;
+        CK(h, cudaMemcpyAsync(lambda, h->lacc, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s));
+        if (st) *st = S;
+        return S.status;
+    }
     double rn = bn;
     const double target = h->opt.adjoint_rtol * bn;
     const double inner = is_mixed(h) ? std::max(h->opt.adjoint_rtol, 1e-4) : h->opt.adjoint_rtol;
@@ -1049,6 +1071,18 @@ extern "C" int sim_kernel_timing(const sim_handle *h, double *hvp_tile_ms, int64
     if (!h) return SIM_EINVAL;
     if (hvp_tile_ms) *hvp_tile_ms = h->t_hvp_ms;
     if (hvp_launches) *hvp_launches = h->n_hvp_timed;
+    return SIM_OK;
+}
+
+extern "C" int sim_set_wait_limit(sim_handle *h, int polls)
+{
+    CHECK_H(h);
+    const int v = polls < 0 ? TileDev{}.wait_polls : polls;
+    if (v != h->ctx.td.wait_polls) {
+        CK(h, cudaDeviceSynchronize());  // no captured graph may still be running
+        drop_graphs(h);                  // they hold the old limit
+        h->ctx.td.wait_polls = v;
+    }
     return SIM_OK;
 }
 

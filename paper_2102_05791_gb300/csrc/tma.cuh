@@ -73,10 +73,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
     return ok != 0;
 }
 
-// Bounded wait on the barrier phase; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
+// Bounded wait on the barrier phase: at most `polls` polls; returns false
+// when they run out (polls = 0 gives up at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int polls = kWaitLimit)
 {
-    for (int i = 0; i < kWaitLimit; ++i)
+    for (int i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
 }
