@@ -15,7 +15,13 @@ Printed JSON line (rank 0):
              host<->device copies of every step's inputs and outputs;
   roofline   the HVP tile kernel: algorithmic bytes per launch (72 B per tet +
              36 B per vertex) / its mean duration, against the HBM peak;
-  cpu_baseline  the FP64 checker timed on a bounded sample of the same solve.
+  accuracy   the GPU results against the FP64 oracle's own stored solutions
+             (tests/golden): the large body at 1/8 size in both precisions,
+             three bodies of the batch, the 200-step walker's BPTT gradient;
+  cpu_baseline  the FP64 oracle on the host cores: element-HVP/s and
+             gradient evaluations/s on the large body (one core and all
+             cores, one process per core on element slices), and solve wall
+             times (single-threaded) on the small workloads.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank solves its own copy of the workload (no
@@ -59,6 +65,11 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 1,024-body measurement")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the comparison with the stored oracle solutions")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle's 200-step walker BPTT and its 1/8-size large-body solve (minutes)")
+    ap.add_argument("--plain-strata", type=int, default=32,
+                    help="size strata of the batch sampled for the plain per-mesh FP64 comparison")
     return ap.parse_args()
 
 
@@ -87,11 +98,27 @@ def c4_inputs(n_meshes=1024, n_steps=60):
     return probs, x0, a_seq, xbT
 
 
-def run_batched(dev, steps, warmup, plain_sample=8):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _state_err(x, x_ref, X):
+    """max |x - x_ref| over the displacement scale max |x_ref - X|."""
+    return float(np.abs(x - x_ref).max() / np.abs(x_ref - X).max())
+
+
+def run_batched(dev, steps, warmup, n_strata=32):
     """Config 4: one batched launch (forward + BPTT of every body) vs the plain
-    per-mesh FP64 path (sim_rollout + sim_rollout_backward per body) on a
-    sample of bodies spread over the size range.  A solve = one body-step,
-    forward Newton solve plus adjoint solve."""
+    per-mesh FP64 path (sim_rollout + sim_rollout_backward per body).  The
+    plain path is timed on one body per size stratum (the batch sorted by
+    triangle count and cut into n_strata equal groups; the stratum's median
+    body stands for its members), so the estimate of the whole batch's plain
+    time follows the measured cost-vs-size curve instead of assuming it is
+    linear.  A solve = one body-step, forward Newton solve plus adjoint solve.
+    Also compares three bodies with the oracle's stored rollouts."""
     import torch
     from paper_2102_05791_gb300 import api
     probs, x0, a_seq, xbT = c4_inputs()
@@ -124,12 +151,30 @@ def run_batched(dev, steps, warmup, plain_sample=8):
            "bodies_failed": int((mstat[:, 0] != 0).sum()),
            "newton_iters": int(mstat[:, 1].sum()), "cg_iters_fwd": int(mstat[:, 2].sum()),
            "cg_iters_adj": int(mstat[:, 3].sum())}
+    acc = None
+    gpath = os.path.join(GOLDEN, "c4_bodies_oracle.npz")
+    if os.path.exists(gpath):
+        g = np.load(gpath)
+        sx, ab, vb0 = out[0][-1].cpu().numpy(), out[2].cpu().numpy(), out[4].cpu().numpy()
+        vo, eo = bt.vert_offsets, bt.elem_offsets
+        per = []
+        for k, i in enumerate(g["bodies"]):
+            q = probs[i]
+            per.append({"body": int(i), "tris": q.n_elem,
+                        "state_err": _state_err(sx[vo[i]:vo[i + 1]], g[f"xT_{k}"], q.X),
+                        "dLda_rel_l2": _rel(ab[:, eo[i]:eo[i + 1]], g[f"abar_{k}"]),
+                        "dLdv0_rel_l2": _rel(vb0[vo[i]:vo[i + 1]], g[f"vbar0_{k}"])})
+        acc = {"against": "oracle rollouts + BPTT stored in tests/golden/c4_bodies_oracle.npz (Newton 1e-10, "
+                          "adjoints 1e-12)", "bodies": per,
+               "max_dLda_rel_l2": max(b["dLda_rel_l2"] for b in per),
+               "max_state_err": max(b["state_err"] for b in per)}
     bt.close()
-    # plain per-mesh FP64 path on a sample spread over the size range
-    order = np.argsort([p.n_elem for p in probs])
-    pick = order[np.linspace(0, len(order) - 1, plain_sample).astype(int)]
-    t_plain = 0.0
-    for i in pick:
+    # plain per-mesh FP64 path, one body per size stratum
+    order = np.argsort([p.n_elem for p in probs], kind="stable")
+    strata = np.array_split(order, n_strata)
+    t_body, tris, t_est = [], [], 0.0
+    for members in strata:
+        i = members[len(members) // 2]
         p = probs[i]
         sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle,
                             density=p.density, gravity=p.gravity, k_contact=p.k_contact,
@@ -145,21 +190,31 @@ def run_batched(dev, steps, warmup, plain_sample=8):
         xT, vT, ck, _ = sim.rollout(x0i, v0i, ai, ckpt_every=20)
         sim.rollout_backward(ai, ck, 20, xbi, torch.zeros_like(x0i))
         torch.cuda.synchronize()
-        t_plain += time.perf_counter() - t0
+        dt = time.perf_counter() - t0
         sim.close()
-    # scale the sample to the batch by element count (cost grows with size)
-    frac = sum(probs[i].n_elem for i in pick) / sum(p.n_elem for p in probs)
-    plain_s_per_batch = t_plain / frac
-    res["plain_fp64_solves_per_s"] = solves / plain_s_per_batch
-    res["plain_sample"] = f"{plain_sample} bodies at evenly spaced size quantiles, scaled by element count"
+        t_body.append(dt)
+        tris.append(p.n_elem)
+        t_est += dt * len(members)
+    # the batched kernel's time split over bodies in proportion to their triangles
+    share = np.array(tris, dtype=np.float64) / float(bt.E) * (ms / 1e3)
+    ratio = np.array(t_body) / share
+    res["plain_fp64_solves_per_s"] = solves / t_est
+    res["plain_sample"] = (f"{n_strata} size strata of the batch (sorted by triangle count, equal counts), the "
+                           f"median body of each timed through sim_rollout + sim_rollout_backward in FP64 at the "
+                           f"same tolerances; batch time = sum over strata of body time x stratum size")
+    res["plain_body_seconds"] = {"tris": tris, "seconds": [round(t, 4) for t in t_body]}
     res["speedup_vs_plain_fp64"] = res["solves_per_s"] / res["plain_fp64_solves_per_s"]
-    return res
+    res["speedup_per_body"] = {"min": float(ratio.min()), "median": float(np.median(ratio)),
+                               "max": float(ratio.max()),
+                               "note": "plain body time / its triangle share of the batched launch"}
+    return res, acc
 
 
 def run_dynamics(dev):
     """Config 2: 64 x 32 grid (4,096 tris), 200 backward-Euler steps with
     checkpoints every 20, forward + BPTT of the horizontal displacement of
-    the vertex mean w.r.t. the 8 x 200 group activations."""
+    the vertex mean w.r.t. the 8 x 200 group activations (adjoints to 1e-8:
+    at 1e-6 the 200-step group gradient was 1.4e-3 off the oracle's)."""
     import torch
     import synth
     from paper_2102_05791_gb300 import api
@@ -167,7 +222,7 @@ def run_dynamics(dev):
     group = torch.from_numpy(p.extra["group"].astype(np.int64)).to(dev)
     sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle, density=p.density,
                         gravity=p.gravity, k_contact=p.k_contact, contact_power=p.contact_power, dt=p.dt,
-                        precision="mixed", tile_elems="auto", device=dev)
+                        precision="mixed", adjoint_rtol=1e-8, tile_elems="auto", device=dev)
     a_groups = torch.from_numpy(p.extra["a_groups"]).to(dev)
     x0 = torch.from_numpy(p.X).to(dev)
     a_seq = a_groups[:, group].contiguous()
@@ -179,15 +234,71 @@ def run_dynamics(dev):
     xT, vT, ck, st = sim.rollout(x0, torch.zeros_like(x0), a_seq, ckpt_every=20)
     xbT = torch.zeros_like(x0)
     xbT[:, 0] = 1.0 / p.n_vert
-    _, _, ab, stb = sim.rollout_backward(a_seq, ck, 20, xbT, torch.zeros_like(x0))
+    _, vb0, ab, stb = sim.rollout_backward(a_seq, ck, 20, xbT, torch.zeros_like(x0))
     g = torch.zeros_like(a_groups).index_add_(1, group, ab)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    return {"workload": "64x32 grid (4,096 tris), 200 backward-Euler steps, checkpoints every 20, forward + BPTT "
-                        "(after an untimed 20-step warm-up)", "tile_shape": list(sim.tile_shape),
-            "seconds": dt, "steps_per_s": 200 * 2 / dt, "newton_iters": st["newton_iters"] + stb["newton_iters"],
-            "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm())}
+    res = {"workload": "64x32 grid (4,096 tris), 200 backward-Euler steps, checkpoints every 20, forward + BPTT "
+                       "(after an untimed 20-step warm-up)", "tile_shape": list(sim.tile_shape),
+           "adjoint_rtol": 1e-8, "seconds": dt, "steps_per_s": 200 * 2 / dt,
+           "newton_iters": st["newton_iters"] + stb["newton_iters"],
+           "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm())}
+    acc = None
+    gpath = os.path.join(GOLDEN, "c2_bptt_oracle.npz")
+    if os.path.exists(gpath):
+        gg = np.load(gpath)
+        acc = {"against": "oracle 200-step rollout + BPTT stored in tests/golden/c2_bptt_oracle.npz (Newton "
+                          "1e-10, adjoints 1e-12)",
+               "state_err": _state_err(xT.cpu().numpy(), gg["xT"], p.X),
+               "dLda_groups_rel_l2": _rel(g.cpu().numpy(), gg["g_groups"]),
+               "dLdv0_rel_l2": _rel(vb0.cpu().numpy(), gg["vbar0"])}
+    return res, acc
+
+
+def run_accuracy_eighth(dev):
+    """The large body at 1/8 size (393,216 tets): forward solve, adjoint and
+    parameter VJP on the GPU in both precisions, against the oracle's stored
+    x*, lambda and dL/da (Newton to 1e-10, adjoint to 1e-11)."""
+    import torch
+    import synth
+    from paper_2102_05791_gb300 import api
+    gpath = os.path.join(GOLDEN, "c5_eighth_oracle.npz")
+    if not os.path.exists(gpath):
+        return None
+    g = np.load(gpath)
+    p = synth.make_config5(2)
+    out = {"against": "oracle solution stored in tests/golden/c5_eighth_oracle.npz", "workload":
+           "box 4x2x2, 64x32x32 hex x 6 tets (393,216 tets, 70,785 vertices)"}
+    for prec, kw in (("mixed", {"tile_elems": "auto"}), ("fp64", {"adjoint_rtol": 1e-10})):
+        sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle,
+                            density=p.density, gravity=p.gravity, precision=prec, device=dev, **kw)
+        a = torch.from_numpy(p.a).to(dev)
+        tgt = torch.from_numpy(p.target).to(dev)
+        x, st = sim.solve(a)
+        gL = ((x.mean(dim=0) - tgt) / p.n_vert).expand(p.n_vert, p.dim).contiguous()
+        lam, sta = sim.adjoint(x, a, gL)
+        dLda = sim.param_vjp(x, a, lam)
+        xs = x.cpu().numpy()
+        out[prec] = {"state_err": _state_err(xs, p.X + g["u_star"], p.X),
+                     "lambda_rel_l2": _rel(lam.cpu().numpy(), g["lam"]),
+                     "dLda_rel_l2": _rel(dLda.cpu().numpy(), g["dLda"]),
+                     "newton_rtol": 1e-8, "adjoint_rtol": kw.get("adjoint_rtol", 1e-6)}
+        sim.close()
+    return out
+
+
+def run_dot_accuracy(sim, sim64, x, a, dev):
+    """The mixed CG loop's p.Ap (FP32 element quadratic forms, FP32 sums within
+    a tile, compensated sums over the tiles) against the FP64 handle's v.(H v)
+    at the same state and direction (the FP64 kernels match the oracle to
+    1e-12 of the contribution scale)."""
+    import torch
+    v = torch.from_numpy(np.random.default_rng(17).standard_normal(tuple(x.shape)).astype(np.float32)).to(dev)
+    _, q32 = sim.hvp_dot(x, a, v)
+    _, q64 = sim64.hvp_dot(x, a, v.double())
+    return {"cg_dot_rel_err": abs(q32 - q64) / abs(q64),
+            "note": "mixed CG p.Ap vs FP64 v.(H v), large body at the solved state, random direction"}
 
 
 def measured_peaks():
@@ -218,15 +329,17 @@ def kernel_source_hash():
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-def recorded_traffic(workload_name):
+def recorded_traffic(workload_name, tile_shape):
     """DRAM bytes per launch of the HVP tile kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+    summary, only if it was taken on the current kernel source, workload and
+    tile shape (elements per tile, threads); otherwise None."""
     path = os.path.join(ROOT, "profiles", "hvp_tile_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        if d.get("elem_kernels_sha") == kernel_source_hash() and d.get("workload") == workload_name:
+        if (d.get("elem_kernels_sha") == kernel_source_hash() and d.get("workload") == workload_name
+                and [d.get("elems_per_tile"), d.get("threads")] == list(tile_shape)):
             return float(d["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -300,39 +413,154 @@ def combine_ranks(times, counts, world, device):
 
 
 # ---------------------------------------------------------------- reference arm / CPU baseline
+#
+# The FP64 oracle on the host cores.  Its checked code stays single-threaded;
+# the multi-core figures run one process per core, each on a contiguous slice
+# of the large body's elements (the element loop is the whole cost of an HVP
+# or gradient evaluation), started together behind a barrier.
 
-def oracle_sample(p, max_cg):
-    """The FP64 checker on a bounded sample of the same solve: the first Newton
-    step of the quasistatic solve with its CG capped at max_cg iterations."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _slice_worker(kind, wl, lo, hi, reps, barrier, queue):
     import oracle
+    p, _ = workload(wl)
     m = oracle.make_model(p)
+    m = m.replace(T=np.ascontiguousarray(m.T[lo:hi]), Dminv=np.ascontiguousarray(m.Dminv[lo:hi]),
+                  W=np.ascontiguousarray(m.W[lo:hi]), fiber=np.ascontiguousarray(m.fiber[lo:hi]))
+    a = np.ascontiguousarray(p.a[lo:hi])
+    rng = np.random.default_rng(3)
+    x = p.X + 1e-3 * rng.standard_normal(p.X.shape)
+    v = rng.standard_normal(p.X.shape)
+    barrier.wait()
     t0 = time.perf_counter()
-    x, st = m.newton(p.a, rtol=1e-8, max_newton=1, max_cg=max_cg)
-    dt = time.perf_counter() - t0
-    hvps = st["cg_iters_total"]
-    return p.n_elem * hvps / dt, dt, hvps
+    for _ in range(reps):
+        m.hvp(x, a, v) if kind == "hvp" else m.grad(x, a)
+    t1 = time.perf_counter()
+    queue.put((t0, t1, hi - lo))
+
+
+def oracle_rate(kind, n_proc, reps, wl="c5"):
+    """Element evaluations per second of the oracle's HVP ("hvp") or gradient
+    ("grad") on a workload (default the large body, 3,145,728 tets), n_proc
+    processes on element slices: (elements x reps) / (last end - first start)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    ne = workload(wl)[0].n_elem
+    cuts = np.linspace(0, ne, n_proc + 1).astype(int)
+    barrier, queue = ctx.Barrier(n_proc), ctx.Queue()
+    procs = [ctx.Process(target=_slice_worker,
+                         args=(kind, wl, int(cuts[i]), int(cuts[i + 1]), reps, barrier, queue))
+             for i in range(n_proc)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    return sum(r[2] for r in res) * reps / (t1 - t0), t1 - t0
+
+
+def _solve_job(name):
+    """Single-threaded oracle solves of the small workloads (wall seconds)."""
+    import oracle
+    import synth
+    if name in ("c1", "c3", "c5_eighth"):
+        p = {"c1": synth.make_config1, "c3": synth.make_config3,
+             "c5_eighth": lambda: synth.make_config5(2)}[name]()
+        m = oracle.make_model(p)
+        t0 = time.perf_counter()
+        oracle.quasistatic_forward_backward(m, p.a, p.target, rtol=1e-8, adj_rtol=1e-6)
+        return name, time.perf_counter() - t0, None
+    if name == "c2":
+        p = synth.make_config2()
+        m = oracle.make_model(p)
+        a_seq = p.extra["a_groups"][:, p.extra["group"]]
+        t0 = time.perf_counter()
+        xs, vs = oracle.rollout(m, p.X.copy(), np.zeros_like(p.X), a_seq, rtol=1e-8)
+        xb = np.zeros_like(p.X)
+        xb[:, 0] = 1.0 / p.n_vert
+        oracle.rollout_backward(m, xs, vs, a_seq, xb, np.zeros_like(p.X), adj_rtol=1e-8)
+        return name, time.perf_counter() - t0, None
+    # c4: the smallest, 10th- and 25th-percentile bodies, sequentially
+    probs = synth.make_config4(1024, 60)
+    order = np.argsort([q.n_elem for q in probs], kind="stable")
+    tris = []
+    t0 = time.perf_counter()  # the batch's generation is not part of the solves
+    for i in (order[0], order[102], order[256]):
+        q = probs[i]
+        m = oracle.make_model(q)
+        xs, vs = oracle.rollout(m, q.X.copy(), np.zeros_like(q.X), q.extra["a_seq"], rtol=1e-8)
+        xb = np.zeros_like(q.X)
+        xb[:, 0] = 1.0 / q.n_vert
+        oracle.rollout_backward(m, xs, vs, q.extra["a_seq"], xb, np.zeros_like(q.X), adj_rtol=1e-8)
+        tris.append(q.n_elem)
+    return name, time.perf_counter() - t0, tris
+
+
+def cpu_baseline(full=False):
+    """The oracle as it stands, timed on this host: element-HVP/s and
+    gradient evaluations/s on one core and on every core, and single-threaded
+    solve wall times (small workloads in parallel processes, one each)."""
+    import multiprocessing as mp
+    cores = host_cores()
+    t_start = time.perf_counter()
+    hvp1, _ = oracle_rate("hvp", 1, 3)
+    hvpN, _ = oracle_rate("hvp", cores, 3)
+    grad1, _ = oracle_rate("grad", 1, 3)
+    gradN, _ = oracle_rate("grad", cores, 3)
+    jobs = ["c1", "c3", "c4"] + (["c2", "c5_eighth"] if full else [])
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        solved = {n: (t, tr) for n, t, tr in pool.map(_solve_job, jobs)}
+    out = {"value": hvpN, "unit": "elem-HVP/s", "cores": cores, "kind": "oracle",
+           "sample": (f"FP64 oracle HVP on the large body (3,145,728 tets), 3 evaluations per process; {cores} "
+                      f"processes on element slices (one core each) for value, one process for hvp_1core"),
+           "hvp_1core": hvp1, "hvp_all_cores": hvpN,
+           "grad_per_s_1core": grad1 / 3145728.0, "grad_per_s_all_cores": gradN / 3145728.0,
+           "solve_seconds_1core": {
+               "c1_quasistatic_fwd_adj": solved["c1"][0],
+               "c3_quasistatic_fwd_adj": solved["c3"][0],
+               "c4_bodies_60_steps_fwd_bptt": {"tris": solved["c4"][1], "seconds": solved["c4"][0],
+                                               "solves_per_s": 3 * 120 / solved["c4"][0]}},
+           "tolerances": "Newton 1e-8; adjoint 1e-6 (quasistatic) or 1e-8 (dynamics)",
+           "seconds": time.perf_counter() - t_start}
+    if full:
+        out["solve_seconds_1core"]["c2_200_steps_fwd_bptt"] = solved["c2"][0]
+        out["solve_seconds_1core"]["c5_eighth_quasistatic_fwd_adj"] = solved["c5_eighth"][0]
+    return out
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on
+    the same workload.  One step = 3 HVP evaluations of the large body on every
+    core (element slices, one process per core): the oracle's pure
+    element-HVP/s, an upper bound of its whole-step element-HVP/s (a whole
+    step also spends time on gradients, energies and vector work)."""
     if rank != 0:
         return
     p, desc = workload(args.workload)
-    max_cg = 3 if args.workload == "c5" else 20
+    cores = host_cores()
     vals = []
     for i in range(args.warmup + args.steps):
-        v, dt, hvps = oracle_sample(p, max_cg)
+        v, dt = oracle_rate("hvp", cores, 3, args.workload)
         if i >= args.warmup:
             vals.append((v, dt))
     value = statistics.median(v for v, _ in vals)
     ms = 1000.0 * statistics.median(dt for _, dt in vals)
-    sample = (f"first Newton step of the {args.workload} solve with CG capped at {max_cg} iterations "
-              f"({p.n_elem} tets), FP64 checker, single thread")
+    sample = (f"pure HVP evaluations of the {args.workload} workload ({p.n_elem} tets), 3 per step, {cores} "
+              f"processes on element slices (one core each), FP64 oracle")
     line = {"impl": "reference", "metric": "element-HVP/s (fwd Newton-CG + adjoint, whole step)", "value": value,
             "unit": "elem-HVP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
-            "cpu_baseline": {"value": value, "unit": "elem-HVP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "elem-HVP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "elem-HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -445,7 +673,7 @@ def run_ours(args, rank, world, local_rank):
                                f"x 2 flops x {sm_mhz:.0f} MHz"}
     else:
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(args.workload), "kernel": "k_tile_hvp<float,3>",
+                "traffic": recorded_traffic(args.workload, sim.tile_shape), "kernel": "k_tile_hvp<float,3>",
                 "peak_source": peak_kind}
     roof.update({"kernel_ms": tile_ms, "kernel_launches_timed": tile_n,
                  "kernel_timing": "CUDA event nodes around every tile launch in one profiled solve after the timed steps",
@@ -461,7 +689,9 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 HVP/CG vectors, f64 state+gradient+energy+reductions" if args.precision == "mixed" else "f64",
+        "dtype": ("f32 HVP and CG vectors; CG dot products f32 within a tile or block and compensated f32 across "
+                  "them; f64 state, gradient, energies, line search and residual checks")
+                 if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision,
                    "tile_shape": {"elems_per_tile": sim.tile_shape[0], "threads": sim.tile_shape[1],
@@ -481,15 +711,23 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "clocks": clk,
     }
+    accuracy = {}
+    if not args.no_accuracy and args.workload == "c5":
+        # the headline step's CG inner product against the FP64 handle's
+        sim64 = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle,
+                              density=p.density, gravity=p.gravity, precision="fp64", device=dev)
+        xs_last = sim.solve(a)[0]
+        accuracy["cg_dot"] = run_dot_accuracy(sim, sim64, xs_last, a, dev)
+        sim64.close()
+        accuracy["large_body_eighth"] = run_accuracy_eighth(dev)
     if not args.no_batched:
-        line["batched"] = run_batched(dev, max(1, min(args.steps, 3)), 1)
-        line["dynamics"] = run_dynamics(dev)
+        line["batched"], accuracy["batched_bodies"] = run_batched(dev, max(1, min(args.steps, 3)), 1,
+                                                                  args.plain_strata)
+        line["dynamics"], accuracy["walker_bptt"] = run_dynamics(dev)
+    if accuracy:
+        line["accuracy"] = accuracy
     if world == 1 and not args.no_cpu_baseline:
-        max_cg = 8 if args.workload == "c5" else 40
-        v, dt, nh = oracle_sample(p, max_cg)
-        line["cpu_baseline"] = {"value": v, "unit": "elem-HVP/s", "cores": 1, "kind": "oracle",
-                                "sample": f"first Newton step of the same solve, CG capped at {max_cg} iterations "
-                                          f"({nh} HVPs, {dt:.1f} s), FP64 checker, single thread"}
+        line["cpu_baseline"] = cpu_baseline(args.cpu_full)
     print(json.dumps(line), flush=True)
 
 

@@ -163,6 +163,16 @@ int sim_energy_grad(sim_handle *h, const double *x, const double *a, double *E_d
 int sim_hvp(sim_handle *h, const double *x, const double *a, const void *v, void *Hv,
             void *stream);
 
+/* The CG loop's inner product v.(H v) (Eq. matrix-free-dfdx), formed as the
+ * CG loop forms p.Ap: each element's quadratic form v_e.(H_e v_e) plus the
+ * per-vertex terms, summed in FP32 within a tile and with compensated FP32
+ * over the tiles (SIM_PREC_MIXED), or in FP64 throughout (SIM_PREC_FP64).
+ * Diagnostic, to measure that sum's error.  v, Hv: DEVICE [n_vert][dim] in
+ * the HVP precision (as for sim_hvp; Hv receives H v); x, a: DEVICE double;
+ * *vHv: HOST double.  Synchronises the stream. */
+int sim_hvp_dot(sim_handle *h, const double *x, const double *a, const void *v, void *Hv, double *vHv,
+                void *stream);
+
 /* Forward solve.  Quasistatic (dt == 0): x_out = argmin_x E(x, a) (Eq.
  * x1-quasistatic-argmin), started from x_init; x0 and v0 must be NULL.
  * Backward Euler (dt > 0): x_out = argmin 1/2 |x - (x0 + dt v0)|_M^2 +

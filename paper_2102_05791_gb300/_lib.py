@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EINVERTED", -4: "ENOTCO
 
 EXPORTED = [
     "sim_default_options", "sim_create", "sim_destroy", "sim_last_error", "sim_sizes",
-    "sim_energy_grad", "sim_hvp", "sim_newton_solve", "sim_adjoint_solve", "sim_param_vjp", "sim_material_vjp",
+    "sim_energy_grad", "sim_hvp", "sim_hvp_dot", "sim_newton_solve", "sim_adjoint_solve", "sim_param_vjp", "sim_material_vjp",
     "sim_step_forward", "sim_step_backward", "sim_rollout", "sim_rollout_backward",
     "sim_time_hvp", "sim_tile_stats", "sim_counters", "sim_energy_noalloc", "sim_noalloc_last_error",
     "sim_set_kernel_timing", "sim_kernel_timing", "sim_set_wait_limit",
@@ -81,6 +81,7 @@ def load(path: str | None = None):
     L.sim_sizes.argtypes = [H, C.POINTER(i), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sim_energy_grad.argtypes = [H, vp, vp, vp, vp, vp]
     L.sim_hvp.argtypes = [H, vp, vp, vp, vp, vp]
+    L.sim_hvp_dot.argtypes = [H, vp, vp, vp, vp, C.POINTER(d), vp]
     L.sim_newton_solve.argtypes = [H, vp, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_adjoint_solve.argtypes = [H, vp, vp, vp, vp, C.POINTER(SimStats), vp]
     L.sim_param_vjp.argtypes = [H, vp, vp, vp, vp, vp]

@@ -140,6 +140,16 @@ class Simulator:
         self._check("sim_hvp", self._lib.sim_hvp(self._h, _ptr(x), _ptr(a), _ptr(v), _ptr(out), _stream()))
         return out
 
+    def hvp_dot(self, x, a, v):
+        """(H v, v.(H v)) with the inner product formed as the CG loop forms p.Ap."""
+        x, a = self._vec(x), self._elem(a)
+        v = self._vec(v, self.vec_dtype, "v")
+        out = self._empty(self.vec_dtype)
+        q = C.c_double()
+        self._check("sim_hvp_dot", self._lib.sim_hvp_dot(self._h, _ptr(x), _ptr(a), _ptr(v), _ptr(out), C.byref(q),
+                                                         _stream()))
+        return out, q.value
+
     def material_vjp(self, x_star, a, lam):
         """Per-element (dL/dmu, dL/dlambda, dL/dk) for adjoint lam at x_star."""
         x_star, a, lam = self._vec(x_star), self._elem(a), self._vec(lam, name="lambda")

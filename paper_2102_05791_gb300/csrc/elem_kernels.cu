@@ -638,14 +638,15 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     }
     const T mu = pick<T>(ph.mu, ph.mu_f), lam = pick<T>(ph.lam, ph.lam_f);
     const T sel = pick<T>(ph.s_el, ph.s_el_f), kk = pick<T>(ph.k, ph.k_f);
-    T qsum = T(0);  // CG: sum of the element quadratic forms v_e . (H_e v_e) of this thread
+    // CG: p.Ap of this tile from the element quadratic forms v_e . (H_e v_e)
+    // and the owners' vertex terms, in the kernel's precision.  In the mixed
+    // kernel the per-thread and block sums stay plain FP32 (GB300's FP64 pipe
+    // runs at 1/64 of FP32, and compensating them here cost ~7 % of the
+    // kernel's time); k_cg_alpha sums the tiles' partials with compensation.
+    T dot = T(0);
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x)
-        hvp_element<T, D, CG, SPRING, RS>(sRec + le * RS, le, sConn[le], suv, ph, mu, lam, sel, kk, qsum);
+        hvp_element<T, D, CG, SPRING, RS>(sRec + le * RS, le, sConn[le], suv, ph, mu, lam, sel, kk, dot);
     __syncthreads();
-    // p.Ap of this thread in the kernel's precision: in the mixed kernel the
-    // block sum stays FP32 too (GB300's FP64 pipe runs at 1/64 of FP32) and
-    // the tile partials are summed with compensation by k_cg_alpha.
-    T dot = qsum;
     for (int k = threadIdx.x; k < nlv; k += blockDim.x)
         hvp_vertex<T, D, CG>(sCode[k], sLinc[k], sGid[k], suv + k * 2 * D, sInc, sRec, vd, ph, y, hp, dot);
     pdl_trigger();  // the alpha reduction may be scheduled once every tile is done
@@ -884,7 +885,9 @@ size_t hvp_smem(const Ctx &c)
 }
 
 // Resident CTAs per SM that the tile's shared memory allows (at most 4);
-// the kernel variant compiled for that count caps registers to match.
+// the kernel variant compiled for that count caps registers to match.  (At
+// 128 threads and 7 resident tiles, the 64-register FP32 variant measured
+// faster in-solve than the 72-register one: 66.3 vs 68.4 us on the large body.)
 template <typename T>
 int hvp_blocks_per_sm(const Ctx &c)
 {

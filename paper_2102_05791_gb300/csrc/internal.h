@@ -121,6 +121,7 @@ struct DevScalars {
     double rr, tol2, pAp, alpha, beta;
     float alpha_f, beta_f;  // FP32 copies of alpha and beta for the FP32 vector kernels
     int iter, max_iter, done, negcurv;
+    int cg_rounds, cg_max_rounds;  // body rounds of the device-side CG loop and their cap
     // Newton
     double gn2;      // |g|^2 of the FP64 gradient
     double gd;       // g . d
@@ -200,7 +201,11 @@ void launch_material_vjp(const Ctx &c, const Phys &ph, const double *u, const do
 // ---------------------------------------------------------------- vector kernels (vec_kernels.cu)
 template <typename T>
 void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p, double rtol,
-                    int max_iter, cudaStream_t s);
+                    int max_iter, int max_rounds, cudaStream_t s);
+// Condition of the device-side CG loop (last node of a WHILE body): go on
+// while CG runs, no kernel gave up on a wait, and fewer than max_rounds
+// bodies have run.
+void launch_cg_cond(const Ctx &c, cudaGraphConditionalHandle hnd, cudaStream_t s);
 // CG update that first completes A p: vertices of one tile take it from Ap
 // (written by the HVP tile kernel), halo vertices add their partial sums hp
 // and their per-vertex terms; then d += alpha p, r -= alpha A p, r.r, beta.
@@ -216,6 +221,9 @@ template <typename T>
 void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s);
 template <typename T>
 void launch_dir_check(const Ctx &c, const double *g, T *d, cudaStream_t s);
+// *out = sum of the HVP tile kernel's v.Av partials, summed as k_cg_alpha does
+template <typename T>
+void launch_tile_dot(const Ctx &c, double *out, cudaStream_t s);
 template <typename T>
 void launch_step_update(const Ctx &c, double *u, const T *d, double t, float *u32, cudaStream_t s);
 

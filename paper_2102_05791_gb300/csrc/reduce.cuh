@@ -72,6 +72,83 @@ __device__ __forceinline__ void ds_merge(float &hi, float &lo, float h2, float l
     two_sum(s, e, hi, lo);
 }
 
+// Running sum of one thread's terms: compensated (TwoSum, error carried in
+// lo) in FP32, plain in FP64.
+template <typename T>
+struct CompSum;
+template <>
+struct CompSum<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo += e;
+    }
+};
+template <>
+struct CompSum<double> {
+    double hi = 0.0, lo = 0.0;
+    __device__ __forceinline__ void add(double x) { hi += x; }
+};
+
+// Compensated FP32 sum over the block of per-thread (hi, lo) pairs, merged
+// in a fixed order; the renormalised pair is valid in thread 0.
+__device__ __forceinline__ float2 block_sum_comp(float hi, float lo)
+{
+    __shared__ float rh[32], rl[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        ds_merge(hi, lo, h2, l2);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        rh[w] = hi;
+        rl[w] = lo;
+    }
+    __syncthreads();
+    float2 r = make_float2(0.0f, 0.0f);
+    if (w == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        hi = in ? rh[lane] : 0.0f;
+        lo = in ? rl[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+            ds_merge(hi, lo, h2, l2);
+        }
+        r = make_float2(hi, lo);
+    }
+    return r;
+}
+
+// Fixed-order compensated sum of n (hi, lo) FP32 partial pairs; valid (as
+// FP64, hi + lo) in thread 0.
+__device__ __forceinline__ double sum_partials(const float2 *p, int n)
+{
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    const int bd = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 3 * bd < n; i += 4 * bd) {
+        float2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __ldcg(p + i + k * bd);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ds_merge(hi[k], lo[k], v[k].x, v[k].y);
+    }
+    for (; i < n; i += bd) {
+        const float2 v = __ldcg(p + i);
+        ds_merge(hi[0], lo[0], v.x, v.y);
+    }
+#pragma unroll
+    for (int k = 1; k < 4; ++k) ds_merge(hi[0], lo[0], hi[k], lo[k]);
+    const float2 r = block_sum_comp(hi[0], lo[0]);
+    return (double)r.x + (double)r.y;
+}
+
 // Fixed-order compensated sum of n FP32 partials; valid (as FP64) in thread 0.
 __device__ __forceinline__ double sum_partials(const float *p, int n)
 {
@@ -150,6 +227,21 @@ __device__ __forceinline__ double block_min(double v)
     return r;
 }
 
+// Block partial of a per-thread running sum into *slot (thread 0): a
+// compensated (hi, lo) pair in FP32, stored as one float2 in the 8-byte
+// slot, or a double in FP64.
+template <typename T>
+__device__ __forceinline__ void store_block_partial(const CompSum<T> &acc, double *slot)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = block_sum_comp(acc.hi, acc.lo);
+        if (threadIdx.x == 0) *reinterpret_cast<float2 *>(slot) = r;
+    } else {
+        const double r = block_sum(acc.hi);
+        if (threadIdx.x == 0) *slot = r;
+    }
+}
+
 // Call after thread 0 has written this block's partial(s).  Returns true in
 // every thread of the block that arrives last; that block resets the ticket.
 // Only the partials (written by thread 0) must be visible to the last block,
@@ -188,6 +280,16 @@ __device__ __forceinline__ double sum_partials(const double *p, int n)
     for (; i < n; i += bd) acc[0] += __ldcg(p + i);
     const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     return block_sum(s);
+}
+
+// Fixed-order sum of n block partials written by store_block_partial<T>.
+template <typename T>
+__device__ __forceinline__ double sum_block_partials(const double *p, int n)
+{
+    if constexpr (sizeof(T) == 4)
+        return sum_partials(reinterpret_cast<const float2 *>(p), n);
+    else
+        return sum_partials(p, n);
 }
 
 __device__ __forceinline__ double min_partials(const double *p, int n)

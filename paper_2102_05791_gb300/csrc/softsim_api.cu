@@ -24,11 +24,19 @@ using namespace softsim;
 namespace {
 
 thread_local std::string g_create_error;
-constexpr int kCgBlock = 16;  // CG iterations per captured graph
+constexpr int kCgBlock = 16;  // CG iterations per captured graph (host-driven loop)
+constexpr int kCgBody = 8;    // CG iterations per round of the device-side loop
 
 struct Graph {
     cudaGraphExec_t exec = nullptr;
     bool valid = false;
+};
+
+// The whole CG solve as one graph: a WHILE conditional node whose body runs
+// kCgBody iterations and then sets the condition on the device.
+struct WhileGraph {
+    cudaGraphExec_t exec = nullptr;
+    int state = 0;  // 0: not built yet, 1: built, -1: refused by this CUDA build (host-driven loop instead)
 };
 
 }  // namespace
@@ -56,6 +64,7 @@ struct sim_handle {
     cudaStream_t cap = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     Graph cg_graph[2][2];           // [dyn][kernel timing]
+    WhileGraph cg_while[2];         // [dyn]
     int timing = 0;                 // record events around HVP tile launches in solves
     cudaEvent_t tev[2 * kCgBlock] = {};
     double t_hvp_ms = 0.0;          // accumulated in-solve HVP tile-kernel time
@@ -151,6 +160,11 @@ static void drop_graphs(sim_handle *h)
             gr.exec = nullptr;
             gr.valid = false;
         }
+    for (auto &wg : h->cg_while) {
+        if (wg.exec) cudaGraphExecDestroy(wg.exec);
+        wg.exec = nullptr;
+        wg.state = 0;
+    }
 }
 
 static bool is_mixed(const sim_handle *h) { return h->precision == SIM_PREC_MIXED; }
@@ -202,9 +216,7 @@ extern "C" int sim_tile_stats(const sim_handle *h, int *n_tiles, double *ept, do
 extern "C" int sim_destroy(sim_handle *h)
 {
     if (!h) return SIM_EINVAL;
-    for (auto &row : h->cg_graph)
-        for (auto &gr : row)
-            if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    drop_graphs(h);
     for (auto &e : h->tev)
         if (e) cudaEventDestroy(e);
     for (void *p : h->allocs) cudaFree(p);
@@ -517,11 +529,11 @@ static int set_state(sim_handle *h, const double *x, bool pin, cudaStream_t s)
 // ---------------------------------------------------------------- CG
 
 template <typename T>
-static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s)
+static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s, int n_iter = kCgBlock, bool pdl = true)
 {
     T *d = (T *)h->vd, *r = (T *)h->vr, *p = (T *)h->vp, *Ap = (T *)h->vAp;
-    h->ctx.pdl = true;  // programmatic edges between the kernels of the captured block
-    for (int k = 0; k < kCgBlock; ++k) {
+    h->ctx.pdl = pdl;  // programmatic edges between the kernels of the captured block
+    for (int k = 0; k < n_iter; ++k) {
         // the timing events bracket the HVP tile kernel alone
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
         launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
@@ -557,13 +569,87 @@ static int get_cg_graph(sim_handle *h, const Phys &ph, cudaGraphExec_t *exec)
     return SIM_OK;
 }
 
-// Runs CG blocks until the device raises `done`.  Returns the iteration count
-// through sc_host->iter.
+// Builds the device-side CG loop: graph = WHILE(cond) { kCgBody iterations;
+// k_cg_cond }, the condition starting at 1 on every launch.
+template <typename T>
+static cudaError_t build_cg_while(sim_handle *h, const Phys &ph, bool pdl, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle hnd = 0;
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams np = {};
+    e = cudaGraphConditionalHandleCreate(&hnd, g, 1u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hnd;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_cg_block<T>(h, ph, h->cap, kCgBody, pdl);
+            launch_cg_cond(h->ctx, hnd, h->cap);
+            const cudaError_t e1 = cudaGetLastError();
+            cudaGraph_t cap_out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(h->cap, &cap_out);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+// The device-side CG loop of this handle (PDL edges inside the body if the
+// CUDA build accepts them), or null if conditional nodes are refused.
+template <typename T>
+static cudaGraphExec_t get_cg_while(sim_handle *h, const Phys &ph)
+{
+    WhileGraph &wg = h->cg_while[ph.dyn ? 1 : 0];
+    if (wg.state == 0) {
+        cudaError_t e = build_cg_while<T>(h, ph, true, &wg.exec);
+        if (e != cudaSuccess) e = build_cg_while<T>(h, ph, false, &wg.exec);
+        wg.state = e == cudaSuccess ? 1 : -1;
+        if (e != cudaSuccess) {
+            wg.exec = nullptr;
+            if (h->verbose)
+                fprintf(stderr, "[softsim] device-side CG loop unavailable (%s); host-driven blocks\n",
+                        cudaGetErrorString(e));
+        }
+    }
+    return wg.state == 1 ? wg.exec : nullptr;
+}
+
+// Rounds of the device-side loop that cover max_iter iterations, plus slack.
+static int cg_max_rounds(int max_iter) { return max_iter / kCgBody + 2; }
+
+// Runs CG until the device raises `done`: one launch of the device-side loop
+// (a single host synchronisation), or, with in-solve kernel timing on or
+// without conditional graph nodes, replays of a kCgBlock-iteration graph with
+// a host check between replays.  Returns the iteration count through
+// sc_host->iter.
 template <typename T>
 static int run_cg(sim_handle *h, const Phys &ph, int max_iter, cudaStream_t s)
 {
+    int rc;
+    if (!h->timing) {
+        cudaGraphExec_t wexec = get_cg_while<T>(h, ph);
+        if (wexec) {
+            CK(h, cudaGraphLaunch(wexec, s));
+            if ((rc = read_scalars(h, s))) return rc;
+            h->ctx.n_launch += (int64_t)h->sc_host->cg_rounds * (5 * kCgBody + 1);
+            if (!h->sc_host->done) return fail(h, SIM_ECUDA, "CG control did not terminate");
+            return SIM_OK;
+        }
+    }
     cudaGraphExec_t exec;
-    int rc = get_cg_graph<T>(h, ph, &exec);
+    rc = get_cg_graph<T>(h, ph, &exec);
     if (rc) return rc;
     if ((rc = read_scalars(h, s))) return rc;
     const int max_blocks = max_iter / kCgBlock + 2;
@@ -626,7 +712,8 @@ static int newton_impl(sim_handle *h, bool dyn, sim_solve_stats *st, cudaStream_
         }
         if (it >= h->opt.max_newton) break;
         const double eta = std::min(h->opt.newton_forcing, std::sqrt(gn / g0));
-        launch_cg_init<T>(c, h->g, -1.0, (T *)h->vd, (T *)h->vr, (T *)h->vp, eta, h->opt.max_cg, s);
+        launch_cg_init<T>(c, h->g, -1.0, (T *)h->vd, (T *)h->vr, (T *)h->vp, eta, h->opt.max_cg,
+                          cg_max_rounds(h->opt.max_cg), s);
         CKL(h);
         if ((rc = run_cg<T>(h, ph, h->opt.max_cg, s))) return rc;
         S.cg_iters_total += h->sc_host->iter;
@@ -742,7 +829,7 @@ static int adjoint_impl(sim_handle *h, bool dyn, const double *b, double *lambda
         }
         if (budget <= 0) break;
         launch_cg_init<T>(c, h->r64, 1.0, (T *)h->vd, (T *)h->vr, (T *)h->vp, std::max(inner, 0.5 * target / rn),
-                          budget, s);
+                          budget, cg_max_rounds(budget), s);
         CKL(h);
         if ((rc = run_cg<T>(h, ph, budget, s))) return rc;
         const int it = h->sc_host->iter;
@@ -817,6 +904,38 @@ extern "C" int sim_hvp(sim_handle *h, const double *x, const double *a, const vo
         launch_hvp<double>(h->ctx, ph, h->u, (const double *)v, (double *)Hv, h->hp64, s);
     CKL(h);
     return SIM_OK;
+}
+
+template <typename T>
+static int hvp_dot_impl(sim_handle *h, const void *v, void *Hv, double *vHv, cudaStream_t s)
+{
+    Ctx &c = h->ctx;
+    const Phys ph = make_phys(h, false);
+    const int64_t nd = c.nv * c.dim;
+    T *p = (T *)h->vp, *Ap = (T *)h->vAp;
+    CK(h, cudaMemcpyAsync(p, v, sizeof(T) * nd, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemsetAsync(&h->sc->done, 0, sizeof(int), s));  // the CG tile kernel skips its work once CG is done
+    launch_hvp_cg<T>(c, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
+    launch_hvp_finalize_only<T>(c, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
+    launch_tile_dot<T>(c, &h->sc->pAp, s);
+    CKL(h);
+    CK(h, cudaMemcpyAsync(Hv, Ap, sizeof(T) * nd, cudaMemcpyDeviceToDevice, s));
+    int rc = read_scalars(h, s);
+    if (rc) return rc;
+    *vHv = h->sc_host->pAp;
+    return SIM_OK;
+}
+
+extern "C" int sim_hvp_dot(sim_handle *h, const double *x, const double *a, const void *v, void *Hv, double *vHv,
+                           void *stream)
+{
+    CHECK_H(h);
+    if (!x || !a || !v || !Hv || !vHv) return fail(h, SIM_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = set_state(h, x, false, s))) return rc;
+    if ((rc = set_activation(h, a, s))) return rc;
+    return is_mixed(h) ? hvp_dot_impl<float>(h, v, Hv, vHv, s) : hvp_dot_impl<double>(h, v, Hv, vHv, s);
 }
 
 extern "C" int sim_newton_solve(sim_handle *h, const double *x_init, const double *a, const double *x0,

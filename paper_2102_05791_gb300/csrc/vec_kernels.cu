@@ -6,9 +6,11 @@
 // k_cg_update_halo and k_cg_beta form r.r and beta and raise `done`, so a
 // whole block of iterations runs without a host round trip and can be
 // captured in a CUDA graph.  Reductions are fixed-order; vectors are float
-// (mixed precision) or double.  In the float CG loop the block partials are
-// FP32 and the one-block sums over them are compensated FP32 (GB300's FP64
-// rate is 1/64 of FP32); everything else is summed in FP64.
+// (mixed precision) or double.  In the float CG loop (GB300's FP64 rate is
+// 1/64 of FP32) r.r is summed in compensated FP32 at every level above a
+// single term (per thread, over a block, over the blocks' (hi, lo) pairs);
+// p.Ap is summed in plain FP32 within a tile (inside the HVP tile kernel)
+// and with compensation over the tiles.  The double loop sums in FP64.
 #include "internal.h"
 #include "reduce.cuh"
 #include "pdl.cuh"
@@ -26,7 +28,8 @@ static inline int vec_grid(int64_t n)
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__restrict__ b, double sign,
                                                  T *__restrict__ d, T *__restrict__ r, T *__restrict__ p, double rtol,
-                                                 int max_iter, double *__restrict__ partials, DevScalars *sc)
+                                                 int max_iter, int max_rounds, double *__restrict__ partials,
+                                                 DevScalars *sc)
 {
     double rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -49,8 +52,18 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__rest
             sc->alpha = sc->beta = sc->pAp = 0.0;
             sc->alpha_f = sc->beta_f = 0.0f;
             sc->done = (tot <= sc->tol2 || max_iter <= 0 || !isfinite(tot)) ? 1 : 0;
+            sc->cg_rounds = 0;
+            sc->cg_max_rounds = max_rounds;
         }
     }
+}
+
+// Sets the WHILE condition of the device-side CG loop after each body round;
+// the round cap ends the loop even if `done` were never raised.
+__global__ void k_cg_cond(cudaGraphConditionalHandle hnd, DevScalars *sc)
+{
+    const int r = ++sc->cg_rounds;
+    cudaGraphSetConditional(hnd, (!sc->done && !sc->kerr && r < sc->cg_max_rounds) ? 1u : 0u);
 }
 
 // d += alpha p, r -= alpha A p, r.r -> beta / done, with A p completed here for
@@ -68,7 +81,7 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
     const bool first = sc->iter == 0;
     const T alpha = pick<T>(sc->alpha, sc->alpha_f);
     const bool contact = ph.kc > 0.0;
-    float rr32 = 0.0f;  // at most a few vertices per thread; block-summed (FP32 loop: compensated across blocks)
+    CompSum<T> rr;  // r.r of this thread's vertices (compensated in FP32)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vd.nv;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (neg) {
@@ -110,27 +123,21 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
             d[i * D + c] += alpha * p[i * D + c];
             const T ri = r[i * D + c] - alpha * a[c];
             r[i * D + c] = ri;
-            rr32 += (float)ri * (float)ri;
+            rr.add(ri * ri);
         }
     }
-    if constexpr (sizeof(T) == 4) {  // FP32 partials, summed with compensation by k_cg_beta<float>
-        const float s = block_sum(rr32);
-        if (threadIdx.x == 0) reinterpret_cast<float *>(partials)[blockIdx.x] = s;
-    } else {
-        const double s = block_sum((double)rr32);
-        if (threadIdx.x == 0) partials[blockIdx.x] = s;  // reduced by k_cg_beta<double>
-    }
+    store_block_partial<T>(rr, partials + blockIdx.x);  // reduced by k_cg_beta<T>
 }
 
 // One block: p.Ap from the HVP tile partials -> alpha (or non-positive curvature).
-// PT is the partials' type (float: compensated FP32 sum).
-template <typename PT>
+// T is the CG precision (float: FP32 tile partials, summed with compensation).
+template <typename T>
 __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ partials, int n, DevScalars *sc)
 {
     pdl_trigger();
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
-    const double pAp = sum_partials(reinterpret_cast<const PT *>(partials), n);
+    const double pAp = sum_partials(reinterpret_cast<const T *>(partials), n);
     if (threadIdx.x == 0) {
         sc->pAp = pAp;
         if (pAp > 0.0 && isfinite(pAp)) {
@@ -144,14 +151,23 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double *__restrict__ pa
     }
 }
 
+// One block: the HVP tile kernel's v.Av partials summed as k_cg_alpha sums
+// them, into *out (for sim_hvp_dot).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tile_dot(const double *__restrict__ partials, int n, double *out)
+{
+    const double v = sum_partials(reinterpret_cast<const T *>(partials), n);
+    if (threadIdx.x == 0) *out = v;
+}
+
 // One block: r.r from the update partials -> beta, iteration count, done.
-template <typename PT>
+template <typename T>
 __global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ partials, int n, DevScalars *sc)
 {
     pdl_trigger();
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
-    const double tot = sum_partials(reinterpret_cast<const PT *>(partials), n);
+    const double tot = sum_block_partials<T>(partials, n);
     if (threadIdx.x == 0) {
         if (sc->negcurv) {
             sc->done = 1;
@@ -368,11 +384,16 @@ void launch_accumulate(const Ctx &c, double *x, const T *d, cudaStream_t s)
 
 template <typename T>
 void launch_cg_init(const Ctx &c, const double *b, double sign, T *d, T *r, T *p, double rtol, int max_iter,
-                    cudaStream_t s)
+                    int max_rounds, cudaStream_t s)
 {
     c.n_launch += 1;
     const int64_t n = c.nv * c.dim;
-    k_cg_init<T><<<vec_grid(n), 256, 0, s>>>(n, b, sign, d, r, p, rtol, max_iter, c.partials, c.sc);
+    k_cg_init<T><<<vec_grid(n), 256, 0, s>>>(n, b, sign, d, r, p, rtol, max_iter, max_rounds, c.partials, c.sc);
+}
+
+void launch_cg_cond(const Ctx &c, cudaGraphConditionalHandle hnd, cudaStream_t s)
+{
+    k_cg_cond<<<1, 1, 0, s>>>(hnd, c.sc);
 }
 
 template <typename T>
@@ -403,6 +424,13 @@ void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s)
     c.n_launch += 1;
     const int64_t n = c.nv * c.dim;
     launch_k(c.pdl, k_cg_dir<T>, dim3(vec_grid(n)), dim3(256), 0, s, n, p, (const T *)r, (const DevScalars *)c.sc);
+}
+
+template <typename T>
+void launch_tile_dot(const Ctx &c, double *out, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_tile_dot<T><<<1, 1024, 0, s>>>(c.partials, c.td.n_tiles, out);
 }
 
 template <typename T>
@@ -490,12 +518,14 @@ void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, d
 int vec_grid_size(int64_t n) { return vec_grid(n); }
 
 #define INST(T)                                                                                                     \
-    template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, cudaStream_t); \
+    template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, int,            \
+                                    cudaStream_t);                                                                \
     template void launch_cg_update_halo<T>(const Ctx &, const Phys &, const T *, T *, T *, const T *, const T *,    \
                                            const T *, cudaStream_t);                                                \
     template void launch_cg_dir<T>(const Ctx &, T *, const T *, cudaStream_t);                                      \
     template void launch_cg_alpha<T>(const Ctx &, int, cudaStream_t);                                               \
     template void launch_dir_check<T>(const Ctx &, const double *, T *, cudaStream_t);                              \
+    template void launch_tile_dot<T>(const Ctx &, double *, cudaStream_t);                                          \
     template void launch_step_update<T>(const Ctx &, double *, const T *, double, float *, cudaStream_t);           \
     template void launch_gather_elem<T>(const Ctx &, const double *, T *, cudaStream_t, int64_t);                   \
     template void launch_accumulate<T>(const Ctx &, double *, const T *, cudaStream_t);

@@ -95,3 +95,23 @@ def test_thousand_body_batch_full_size():
         assert np.linalg.norm(abar[:, eo[i]:eo[i + 1]] - ab) <= 1e-4 * np.linalg.norm(ab), p.name
         assert np.linalg.norm(vb0[vs_:ve_] - vb) <= 1e-4 * np.linalg.norm(vb), p.name
     b.close()
+
+
+def test_cg_inner_product_error_against_fp64():
+    """The mixed CG loop's p.Ap on the large 3D body in the benchmark's launch
+    configuration: FP32 element quadratic forms, plain FP32 sums within each
+    384-tet tile, compensated FP32 sums over the 8,192 tiles.  Against the
+    FP64 v.(H v) of the oracle (which also carries the FP32 HVP's own
+    rounding), and against the FP64 dot of the kernel's own FP32 H v (the
+    summation alone); both within 1e-5 relative."""
+    p = synth.make_config5()
+    sim = make_sim(p, "mixed", tile_elems="auto")
+    m = oracle.make_model(p)
+    x = deformed(p, 0.005, seed=15)
+    v = np.random.default_rng(17).standard_normal(x.shape).astype(np.float32).astype(np.float64)
+    Hv, q = sim.hvp_dot(dev(x), dev(p.a), dev(v, sim.vec_dtype))
+    q64 = float(np.dot(v.ravel(), m.hvp(x, p.a, v).ravel()))
+    assert q64 > 0.0
+    assert abs(q - q64) <= 1e-5 * q64, (q, q64)
+    q_own = float(np.dot(v.ravel(), host(Hv).astype(np.float64).ravel()))
+    assert abs(q - q_own) <= 1e-5 * abs(q_own), (q, q_own)
