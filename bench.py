@@ -314,8 +314,8 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("elem_kernels.cu", "tiling.cpp", "elem_math.cuh", "layout.h", "tma.cuh", "reduce.cuh", "pdl.cuh",
-                  "internal.h")
+KERNEL_SOURCES = ("elem_kernels.cu", "tiling.cpp", "elem_math.cuh", "tile_device.cuh", "layout.h", "tma.cuh",
+                  "reduce.cuh", "pdl.cuh", "internal.h")
 
 
 def kernel_source_hash():

@@ -58,6 +58,7 @@ enum {
 enum { SIM_PREC_FP64 = 0, SIM_PREC_MIXED = 1 };
 enum { SIM_LOG_EXACT = 0, SIM_LOG_QUAD = 1 };
 enum { SIM_MUSCLE_CONTRACTILE = 0, SIM_MUSCLE_SPRING = 1 };
+enum { SIM_CG_AUTO = 0, SIM_CG_ITERATION = 1 };
 
 typedef struct sim_handle sim_handle;
 
@@ -117,6 +118,10 @@ typedef struct {
     int max_ls;               /* backtracking halvings cap */
     int tile_elems;           /* elements per tile (0 = library default) */
     int threads;              /* threads per element-kernel block (0 = default) */
+    int cg_kernel;            /* SIM_CG_AUTO: a whole CG solve in one cooperative
+                                 kernel when every tile of the mesh fits on the GPU
+                                 at once, else per-iteration kernels;
+                                 SIM_CG_ITERATION: always per-iteration kernels */
 } sim_options;
 
 typedef struct {
@@ -129,7 +134,8 @@ typedef struct {
 } sim_solve_stats;
 
 /* Fill `opt` with the defaults (MIXED, rtol 1e-8, forcing cap 0.5, adjoint
- * 1e-6, 100 Newton, 500 CG, 4 n_dof adjoint CG cap, 30 halvings). */
+ * 1e-6, 100 Newton, 500 CG, 4 n_dof adjoint CG cap, 30 halvings,
+ * SIM_CG_AUTO). */
 int sim_default_options(sim_options *opt);
 
 /* Build a handle: validates the mesh (ids in range, positive rest volumes),

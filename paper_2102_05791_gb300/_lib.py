@@ -16,6 +16,7 @@ SIM_OK, SIM_EINVAL, SIM_ECUDA, SIM_EINVERTED, SIM_ENOTCONVERGED, SIM_ELINESEARCH
 SIM_PREC_FP64, SIM_PREC_MIXED = 0, 1
 SIM_LOG_EXACT, SIM_LOG_QUAD = 0, 1
 SIM_MUSCLE_CONTRACTILE, SIM_MUSCLE_SPRING = 0, 1
+SIM_CG_AUTO, SIM_CG_ITERATION = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EINVERTED", -4: "ENOTCONVERGED",
                 -5: "ELINESEARCH", -6: "ENAN", -7: "ENOMEM"}
@@ -47,7 +48,7 @@ class SimOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("newton_rtol", C.c_double), ("newton_forcing", C.c_double),
                 ("adjoint_rtol", C.c_double),
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_adjoint_cg", C.c_int),
-                ("max_ls", C.c_int), ("tile_elems", C.c_int), ("threads", C.c_int)]
+                ("max_ls", C.c_int), ("tile_elems", C.c_int), ("threads", C.c_int), ("cg_kernel", C.c_int)]
 
 
 class SimStats(C.Structure):

@@ -42,13 +42,15 @@ class Simulator:
     include/softsim.h.  Host arrays (numpy or CPU tensors) are copied.
     ``tile_elems="auto"`` (or ``threads="auto"``) picks the tile shape with
     the autotuner (paper_2102_05791_gb300.autotune, cached per GPU).
+    ``cg_kernel="auto"`` runs each CG solve as one cooperative kernel when all
+    tiles fit on the GPU at once; ``"iteration"`` keeps per-iteration kernels.
     """
 
     def __init__(self, X, T, fixed=None, fiber=None, *, mu, lam, k_muscle=0.0, density=0.0, gravity=0.0,
                  k_contact=0.0, contact_power=3, log_mode=0, dt=0.0, k_friction=0.0, eps_friction=0.01, muscle_model=0,
                  precision="mixed", newton_rtol=1e-8, newton_forcing=0.5,
                  adjoint_rtol=1e-6, max_newton=100, max_cg=500, max_adjoint_cg=0, max_ls=30, tile_elems=0,
-                 threads=0, device=None):
+                 threads=0, cg_kernel="auto", device=None):
         self._lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if tile_elems == "auto" or threads == "auto":
@@ -79,6 +81,7 @@ class Simulator:
         opt.newton_forcing = float(newton_forcing)
         opt.max_newton, opt.max_cg, opt.max_adjoint_cg, opt.max_ls = int(max_newton), int(max_cg), int(max_adjoint_cg), int(max_ls)
         opt.tile_elems, opt.threads = int(tile_elems), int(threads)
+        opt.cg_kernel = {"auto": L.SIM_CG_AUTO, "iteration": L.SIM_CG_ITERATION}[cg_kernel]
         self.precision = precision
         self.dt = float(dt)
         self.vec_dtype = torch.float32 if precision == "mixed" else torch.float64

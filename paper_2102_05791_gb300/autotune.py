@@ -3,9 +3,10 @@ batched persistent solver.
 
 For a mesh, tries candidate (elements per tile, threads per block) pairs:
 builds a handle for each, runs a short adjoint CG solve at the rest shape
-with in-solve kernel timing (CUDA events around every HVP tile launch inside
-the captured CG graph), and keeps the pair with the smallest mean launch
-time.  Results are cached in a JSON file keyed by GPU name, dimension,
+(48 iterations, in whichever way the handle runs CG: one cooperative kernel
+when all tiles fit on the GPU, else per-iteration kernels) and keeps the pair
+with the smallest time per CG iteration, measured with CUDA events around the
+solve.  Results are cached in a JSON file keyed by GPU name, dimension,
 element-count bucket (power of two) and precision, so later handles of a
 similar mesh reuse the choice without tuning.
 
@@ -37,7 +38,7 @@ def _key(dim: int, n_elem: int, precision: str, muscle_model: int = 0) -> str:
     name = torch.cuda.get_device_name(torch.cuda.current_device())
     bucket = int(math.log2(max(n_elem, 1)))
     # the spring muscle stages the fiber too (more shared memory per tile)
-    return f"{name}|d{dim}|e2^{bucket}|{precision}" + ("|spring" if muscle_model else "")
+    return f"{name}|d{dim}|e2^{bucket}|{precision}|per-cg-iteration" + ("|spring" if muscle_model else "")
 
 
 def _load() -> dict:
@@ -59,7 +60,7 @@ def _store(cache: dict) -> None:
 
 def measure(X, T, fixed, fiber, tile_elems: int, threads: int, precision: str = "mixed", iters: int = 48,
             **material) -> float:
-    """Mean in-solve HVP tile-kernel time (ms) for one tile shape."""
+    """Time per CG iteration (ms) of a short adjoint solve for one tile shape."""
     import torch
 
     from . import api
@@ -72,19 +73,21 @@ def measure(X, T, fixed, fiber, tile_elems: int, threads: int, precision: str = 
         rng = np.random.default_rng(0)
         b = torch.from_numpy(rng.standard_normal((sim.n_vert, sim.dim))).to(dev)
         sim.adjoint(x, a, b, check=False)  # warm-up: graph capture, module loading
-        sim.set_kernel_timing(True)
-        sim.adjoint(x, a, b, check=False)
         torch.cuda.synchronize()
-        ms, n = sim.kernel_timing()
-        sim.set_kernel_timing(False)
-        return ms / max(n, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        _, st = sim.adjoint(x, a, b, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / max(st["cg_iters_total"], 1)
     finally:
         sim.close()
 
 
 def best_tile_shape(X, T, fixed=None, fiber=None, precision: str = "mixed", candidates=None, use_cache: bool = True,
                     **material):
-    """(tile_elems, threads) with the fastest HVP tile kernel for this mesh."""
+    """(tile_elems, threads) with the fastest CG iteration for this mesh."""
     X = np.asarray(X)
     T = np.asarray(T)
     dim = X.shape[1]

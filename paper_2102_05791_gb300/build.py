@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsoftsim.so")
-SOURCES = ["elem_kernels.cu", "vec_kernels.cu", "softsim_api.cu", "tiling.cpp", "noalloc.cu", "batched.cu"]
+SOURCES = ["elem_kernels.cu", "vec_kernels.cu", "softsim_api.cu", "tiling.cpp", "noalloc.cu", "batched.cu",
+           "cg_coop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

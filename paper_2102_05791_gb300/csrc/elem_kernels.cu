@@ -28,66 +28,9 @@
 #include "tma.cuh"
 #include "elem_math.cuh"
 #include "pdl.cuh"
+#include "tile_device.cuh"
 
 namespace softsim {
-
-// Corner forces of one element into its record (slots corner*D + i; corner
-// 0 takes minus the column sum of G), written as pairs: 8-byte (FP32) or
-// 16-byte (FP64) stores.  rec must be aligned to the pair size.
-template <typename T, int D>
-__device__ __forceinline__ void store_corners(T *rec, const T G[D][D])
-{
-    T out[(D + 1) * D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        T s = T(0);
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            out[(j + 1) * D + i] = G[i][j];
-            s += G[i][j];
-        }
-        out[i] = -s;
-    }
-#pragma unroll
-    for (int q = 0; q < (D + 1) * D / 2; ++q) {
-        if constexpr (sizeof(T) == 4)
-            reinterpret_cast<float2 *>(rec)[q] = make_float2(out[2 * q], out[2 * q + 1]);
-        else
-            reinterpret_cast<double2 *>(rec)[q] = make_double2(out[2 * q], out[2 * q + 1]);
-    }
-}
-
-// Sum of the corners touching a local vertex in a fixed order: the entries
-// of its incidence list at even and at odd positions are summed as two
-// independent chains (two loads in flight per step), then added (inc points
-// at the tile's incidence block, each entry the offset of a corner's D
-// values among the tile's element records; w is the vertex's lv_inc word).
-template <typename T, int D>
-__device__ __forceinline__ void gather_corners(const uint16_t *inc, uint32_t w, const T *scr, T acc[D])
-{
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = T(0);
-    const int s0 = (int)(w & 0xffffu), n = (int)((w >> 16) & kLvCountMask);
-    T acc1[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc1[c] = T(0);
-    int s = s0;
-    for (; s + 1 < s0 + n; s += 2) {
-        const T *p = scr + inc[s], *q = scr + inc[s + 1];
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            acc[c] += p[c];
-            acc1[c] += q[c];
-        }
-    }
-    if (s < s0 + n) {
-        const T *p = scr + inc[s];
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] += p[c];
-    }
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] += acc1[c];
-}
 
 // Per-vertex potential terms: gravity m g y and ground penalty kc max(0,-y)^p.
 __device__ __forceinline__ double pen_pow(double pen, int p) { return p == 2 ? pen * pen : pen * pen * pen; }
@@ -398,141 +341,6 @@ __global__ void __launch_bounds__(256) k_fin_grad(TileDev td, VertDev vd, Phys p
 
 // ---------------------------------------------------------------- HVP
 
-// One element of the HVP: reads the element's record (pair loads) and the
-// staged u and v of its vertices, evaluates G = W dP(dF) Dm^-T plus the
-// muscle term, adds v_e . (H_e v_e) to qsum (CG), and overwrites the record
-// in place with the element's corner forces.
-template <typename T, int D, bool CG, bool SPRING, int RS>
-__device__ __forceinline__ void hvp_element(T *rec, int le, uint32_t cword, const T *suv, const Phys &ph, T mu,
-                                            T lam, T sel, T kk, T &qsum)
-{
-    constexpr int NF = hvp_fields(D, SPRING);
-    int lid[D + 1];
-    unpack<D>(cword, lid);
-    // Dm^-1, g and W first (for the contractile muscle that includes the
-    // activation); the spring's fiber and activation where they are used
-    constexpr int N1 = (FI<D>::W + 2) / 2 * 2;
-    T rv[RS];
-    load_pairs<T, N1>(rec, rv);
-    T B[D][D], Du[D][D], Dv[D][D], F[D][D], dF[D][D], C[D][D], dC[D][D], gv[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) B[i][j] = rv[FI<D>::B + i * D + j];
-#pragma unroll
-    for (int i = 0; i < D; ++i) gv[i] = rv[FI<D>::G + i];
-    const T W = rv[FI<D>::W] * sel;
-    edges_uv<T, D>(suv, lid, Du, Dv);
-    mul<T, D>(Du, B, F, true);
-    mul<T, D>(Dv, B, dF, false);
-    cof<T, D>(F, C);
-    dcof<T, D>(F, dF, dC);
-    const T J = detF<T, D>(F, C);
-    T dJ = T(0);
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) dJ += C[i][j] * dF[i][j];
-    T l, cc, cp;
-    log_terms<T>(ph.log_mode, mu, lam, J, l, cc, cp);
-    const T cpdJ = cp * dJ;
-    T dvg[D];  // (d2psi_m/dq2) dq with dq = dF f = Dv g
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        T s = T(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) s += Dv[i][k] * gv[k];
-        dvg[i] = s;
-    }
-    if constexpr (N1 < RS) load_pairs<T, RS - N1>(rec + N1, rv + N1);
-    const T aval = rv[NF];
-    if constexpr (SPRING) {  // spring, with q = F f = f + Du g
-        T q[D], s2 = T(0), qdq = T(0);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            T s = rv[FI<D>::F + i];
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += Du[i][k] * gv[k];
-            q[i] = s;
-            s2 += s * s;
-            qdq += s * dvg[i];
-        }
-        T c1, c2;
-        spring_terms<T>(W != T(0), kk, aval, sqrt(s2), c1, c2);
-#pragma unroll
-        for (int i = 0; i < D; ++i) dvg[i] = c1 * dvg[i] + c2 * qdq * q[i];
-    } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) dvg[i] *= kk * aval;
-    }
-    T G[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T s = T(0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
-            G[i][j] = W * (s + dvg[i] * gv[j]);
-        }
-    if (CG) {
-        // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) qsum += Dv[i][j] * G[i][j];
-    }
-    store_corners<T, D>(rec + corner_base(le), G);  // overwrites this element's own record only
-}
-
-// One local vertex of the HVP: adds its corners in fixed order, adds the
-// per-vertex terms (contact curvature, inertia, friction) where it owns
-// them, and writes A v (single-tile vertex, masked) or its halo partial; the
-// owner's vertex terms of p.Ap go to dot (CG).  uv: the vertex's staged
-// record [u (D), v (D)].
-template <typename T, int D, bool CG>
-__device__ __forceinline__ void hvp_vertex(int code, uint32_t linc, int64_t gid, const T *uv, const uint16_t *sInc,
-                                           const T *sRec, const VertDev &vd, const Phys &ph, T *__restrict__ y,
-                                           T *__restrict__ hp, T &dot)
-{
-    if (code == LV_PAD) return;
-    T acc[D];
-    gather_corners<T, D>(sInc, linc, sRec, acc);
-    const bool contact = ph.contact != 0, dyn = ph.dyn != 0;
-    const bool interior = code == LV_INTERIOR;
-    const bool owner = CG && (interior || (code & 1));  // counts the vertex terms of p.Ap
-    if ((interior || owner) && (contact || dyn)) {
-        T kcv = T(0), m = T(0), mh = T(0);  // contact curvature and inertia (+ friction) diagonals
-        if (contact) {
-            const double yy = vd.X[gid * D + 1] + (double)uv[1];
-            const double pen = yy < 0.0 ? -yy : 0.0;
-            const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-            kcv = T(ph.s_el * d2);
-        }
-        if (dyn) {
-            m = T(vd.mass[gid]);
-            mh = ph.fw ? m + T(ph.fw[gid]) : m;  // friction stiffens the horizontal axes
-        }
-        T dv[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) dv[c] = (c == 1 ? m + kcv : mh) * uv[D + c];
-        if (interior)
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] += dv[c];
-        if (owner)
-#pragma unroll
-            for (int c = 0; c < D; ++c) dot += dv[c] * uv[D + c];
-    }
-    if (interior) {
-        const bool fx = (linc & kLvPinned) != 0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) y[gid * D + c] = fx ? T(0) : acc[c];
-    } else {
-#pragma unroll
-        for (int c = 0; c < D; ++c) hp[(int64_t)(code >> 1) * D + c] = acc[c];
-    }
-}
-
 // Shared-memory plan of the HVP tile kernel (offsets in bytes, all 16-byte
 // aligned because max_te is a multiple of 8, max_tv of 4 and rs even).
 template <typename T, int D>
@@ -645,7 +453,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     // kernel's time); k_cg_alpha sums the tiles' partials with compensation.
     T dot = T(0);
     for (int le = threadIdx.x; le < ne_t; le += blockDim.x)
-        hvp_element<T, D, CG, SPRING, RS>(sRec + le * RS, le, sConn[le], suv, ph, mu, lam, sel, kk, dot);
+        hvp_element<T, D, CG, SPRING, RS>(sRec + le * RS, le, sConn[le], suv, ph, mu, lam, sel, kk, dot,
+                                          sRec + le * RS);
     __syncthreads();
     for (int k = threadIdx.x; k < nlv; k += blockDim.x)
         hvp_vertex<T, D, CG>(sCode[k], sLinc[k], sGid[k], suv + k * 2 * D, sInc, sRec, vd, ph, y, hp, dot);

@@ -122,6 +122,7 @@ struct DevScalars {
     float alpha_f, beta_f;  // FP32 copies of alpha and beta for the FP32 vector kernels
     int iter, max_iter, done, negcurv;
     int cg_rounds, cg_max_rounds;  // body rounds of the device-side CG loop and their cap
+    unsigned int gs_count, gs_pad;  // grid-barrier word of the cooperative CG kernel (zeroed before each launch)
     // Newton
     double gn2;      // |g|^2 of the FP64 gradient
     double gd;       // g . d
@@ -160,6 +161,7 @@ struct Ctx {
     DevScalars *sc = nullptr;
     mutable int64_t n_launch = 0;  // kernels launched through this context
     mutable bool pdl = false;      // launch CG-loop kernels with programmatic dependent launch
+    mutable int coop_fit[2] = {-1, -1};  // [FP32, FP64] cooperative CG kernel fits: 1 / 0, -1 = not checked
 };
 
 // ---------------------------------------------------------------- launchers
@@ -197,6 +199,16 @@ void launch_param_vjp(const Ctx &c, const Phys &ph, const double *u, const doubl
 // per-element dL/dmu, dL/dlambda, dL/dk (caller order; null outputs skipped)
 void launch_material_vjp(const Ctx &c, const Phys &ph, const double *u, const double *a, const double *lam,
                          double *dmu, double *dlam, double *dk, cudaStream_t s);
+
+// ---------------------------------------------------------------- cooperative CG (cg_coop.cu)
+// Whether every tile can be resident at once for the cooperative CG kernel.
+template <typename T>
+bool cg_coop_fits(const Ctx &c);
+// The CG iterations of one solve in one cooperative launch (after
+// launch_cg_init; results in sc as from the per-iteration kernels).
+template <typename T>
+cudaError_t launch_cg_coop(const Ctx &c, const Phys &ph, const T *u, T *d, T *r, T *p, T *Ap, T *hp,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------- vector kernels (vec_kernels.cu)
 template <typename T>

@@ -147,7 +147,8 @@ static int read_scalars(sim_handle *h, cudaStream_t s)
         // clear the flag so that the handle's next call starts clean
         CK(h, cudaMemsetAsync(&h->sc->kerr, 0, sizeof(int), s));
         CK(h, cudaStreamSynchronize(s));
-        return fail(h, SIM_ECUDA, "a kernel gave up waiting for its bulk copies");
+        return fail(h, SIM_ECUDA, h->sc_host->kerr & 2 ? "a kernel gave up waiting at a grid barrier"
+                                                       : "a kernel gave up waiting for its bulk copies");
     }
     return SIM_OK;
 }
@@ -480,6 +481,8 @@ extern "C" int sim_create(const sim_mesh *mesh, const sim_material *mat, const s
         return fail(nullptr, SIM_EINVAL, "k_friction must be finite and >= 0, eps_friction finite");
     if (opt && opt->precision != SIM_PREC_FP64 && opt->precision != SIM_PREC_MIXED)
         return fail(nullptr, SIM_EINVAL, "precision must be SIM_PREC_FP64 or SIM_PREC_MIXED");
+    if (opt && opt->cg_kernel != SIM_CG_AUTO && opt->cg_kernel != SIM_CG_ITERATION)
+        return fail(nullptr, SIM_EINVAL, "cg_kernel must be SIM_CG_AUTO or SIM_CG_ITERATION");
     sim_handle *h = new sim_handle();
     const int rc = create_impl(h, mesh, mat, opt);
     if (rc != SIM_OK) {
@@ -638,6 +641,11 @@ template <typename T>
 static int run_cg(sim_handle *h, const Phys &ph, int max_iter, cudaStream_t s)
 {
     int rc;
+    if (!h->timing && h->opt.cg_kernel == SIM_CG_AUTO && cg_coop_fits<T>(h->ctx)) {
+        CK(h, launch_cg_coop<T>(h->ctx, ph, View<T>::u(h), (T *)h->vd, (T *)h->vr, (T *)h->vp, (T *)h->vAp,
+                                View<T>::hp(h), s));
+        return read_scalars(h, s);
+    }
     if (!h->timing) {
         cudaGraphExec_t wexec = get_cg_while<T>(h, ph);
         if (wexec) {

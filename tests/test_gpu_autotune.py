@@ -1,5 +1,6 @@
-"""The tile-shape autotuner: picks one of its candidates by in-solve kernel
-timing, caches the choice, and a cached choice is reused without measuring."""
+"""The tile-shape autotuner: picks one of its candidates by the time per CG
+iteration of a short solve, caches the choice, and a cached choice is reused
+without measuring."""
 import pytest
 
 import synth
