@@ -384,29 +384,32 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     const HvpSmem<T, D> L(MTE ? MTE : td.max_te, td.max_tv, RS);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // [0]: vertex tables, [1]: element data
     T *sRec = reinterpret_cast<T *>(smem + L.rec);
-    const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
-    const uint16_t *sInc = reinterpret_cast<const uint16_t *>(smem + L.inc);
-    const int32_t *sGid = reinterpret_cast<const int32_t *>(smem + L.gid);
-    const int32_t *sCode = reinterpret_cast<const int32_t *>(smem + L.code);
-    const uint32_t *sLinc = reinterpret_cast<const uint32_t *>(smem + L.linc);
+    // vertex table: [gid, code, lv_inc] per local vertex (stride 3 words:
+    // a warp's lanes read distinct banks)
+    const int32_t *sLv = reinterpret_cast<const int32_t *>(smem + L.gid);
     T *suv = reinterpret_cast<T *>(smem + L.uv);  // per local vertex: u (D values), then v (D values)
     const int t = blockIdx.x;
-    const int es = td.tile_elem[t], ne_t = td.tile_elem[t + 1] - es;
-    const int vs = td.tile_vert[t], nlv = td.tile_vert[t + 1] - vs;
+    // a tile's ranges: from its index for equal tiles (no dependent load before
+    // the bulk copies can be issued), else from the offset tables
+    const int es = td.uni_te ? t * td.uni_te : td.tile_elem[t];
+    const int ne_t = td.uni_te ? td.uni_te : td.tile_elem[t + 1] - es;
+    const int vs = td.uni_tv ? t * td.uni_tv : td.tile_vert[t];
+    const int nlv = td.uni_tv ? td.uni_tv : td.tile_vert[t + 1] - vs;
+    // the tile's connectivity and incidence block arrive as one blob: conn
+    // [ne_t] then inc [ne_t (D+1)] (both 16-byte multiples)
+    const uint32_t *sConn = reinterpret_cast<const uint32_t *>(smem + L.conn);
+    const uint16_t *sInc = reinterpret_cast<const uint16_t *>(smem + L.conn + (size_t)ne_t * 4);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
-        // vertex tables first: the vertex gather below overlaps the element copy
-        mbar_arrive_expect_tx(bar, 3u * nlv * 4);
-        bulk_g2s(smem + L.gid, td.lv_gid + vs, (uint32_t)nlv * 4, bar);
-        bulk_g2s(smem + L.code, td.lv_code + vs, (uint32_t)nlv * 4, bar);
-        bulk_g2s(smem + L.linc, td.lv_inc + vs, (uint32_t)nlv * 4, bar);
-        const uint32_t brec = (uint32_t)ne_t * RS * sizeof(T);
-        mbar_arrive_expect_tx(bar + 1, brec + (uint32_t)ne_t * 4 + (uint32_t)ne_t * (D + 1) * 2);
+        // vertex table first: the vertex gather below overlaps the element copy
+        mbar_arrive_expect_tx(bar, 12u * nlv);
+        bulk_g2s(smem + L.gid, td.lv3 + (int64_t)vs * 3, 12u * nlv, bar);
+        const uint32_t brec = (uint32_t)ne_t * RS * sizeof(T), bci = (uint32_t)ne_t * (4 + 2 * (D + 1));
+        mbar_arrive_expect_tx(bar + 1, brec + bci);
         const uint64_t pol = l2_evict_first_policy();  // element data is read once per launch
         bulk_g2s_stream(sRec, erec + (int64_t)es * RS, brec, bar + 1, pol);
-        bulk_g2s_stream(smem + L.conn, td.conn + es, (uint32_t)ne_t * 4, bar + 1, pol);
-        bulk_g2s_stream(smem + L.inc, td.inc + (int64_t)es * (D + 1), (uint32_t)ne_t * (D + 1) * 2, bar + 1, pol);
+        bulk_g2s_stream(smem + L.conn, td.ci + (int64_t)es * (4 + 2 * (D + 1)), bci, bar + 1, pol);
     }
     __syncthreads();
     // Everything copied so far is static during a solve; state (u, v) and the
@@ -429,8 +432,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
         return;
     }
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
-        const int64_t gid = sGid[k];
-        const bool fx = (sLinc[k] & kLvPinned) != 0;
+        const int64_t gid = sLv[3 * k];
+        const bool fx = ((uint32_t)sLv[3 * k + 2] & kLvPinned) != 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             suv[k * 2 * D + c] = u[gid * D + c];
@@ -457,7 +460,8 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
                                           sRec + le * RS);
     __syncthreads();
     for (int k = threadIdx.x; k < nlv; k += blockDim.x)
-        hvp_vertex<T, D, CG>(sCode[k], sLinc[k], sGid[k], suv + k * 2 * D, sInc, sRec, vd, ph, y, hp, dot);
+        hvp_vertex<T, D, CG>(sLv[3 * k + 1], (uint32_t)sLv[3 * k + 2], sLv[3 * k], suv + k * 2 * D, sInc, sRec, vd, ph,
+                             y, hp, dot);
     pdl_trigger();  // the alpha reduction may be scheduled once every tile is done
     if (CG) {
         const T sum = block_sum(dot);

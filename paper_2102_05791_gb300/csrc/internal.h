@@ -49,6 +49,10 @@ struct TileDev {
     int max_te = 0, max_tv = 0;
     int n_fin = 0;
     int rs = 0;                          // element-record stride (words), rec_stride(hvp_fields(dim, spring))
+    // when every tile has the same padded element and local-vertex counts
+    // (a regular mesh cut into equal blocks), those counts: a tile's ranges
+    // then follow from its index without loading tile_elem / tile_vert
+    int uni_te = 0, uni_tv = 0;
     const int32_t *tile_elem = nullptr;  // [n_tiles + 1]
     const int32_t *tile_vert = nullptr;  // [n_tiles + 1]
     const int32_t *lv_gid = nullptr;     // [n_lv]
@@ -62,6 +66,10 @@ struct TileDev {
     const int32_t *fin_gid = nullptr;    // [n_fin]
     const int32_t *fin_ptr = nullptr;    // [n_fin + 1]
     const int32_t *vfin = nullptr;       // [nv] halo index of a vertex, -1 if one tile owns it
+    // the same tables packed for the HVP tile kernel's bulk copies:
+    const int32_t *lv3 = nullptr;        // [n_lv][3] gid, code, lv_inc of each local vertex
+    const uint8_t *ci = nullptr;         // per tile at byte es * (4 + 2 (dim+1)): conn [ne_t] u32, then the
+                                         // tile's incidence block [ne_t (dim+1)] u16
     // poll limit of the HVP tile kernel's first bulk-copy wait (the copies of
     // the vertex tables); the library default is the same bound as every
     // other wait, and sim_set_wait_limit lowers it to exercise the error path

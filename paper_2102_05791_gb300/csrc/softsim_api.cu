@@ -391,6 +391,14 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     td.max_tv = tb.max_tv;
     td.n_fin = (int)tb.fin_gid.size();
     td.rs = tb.rs;
+    {
+        bool uni = tb.n_tiles > 0;
+        const int te0 = tb.tile_elem[1] - tb.tile_elem[0], tv0 = tb.tile_vert[1] - tb.tile_vert[0];
+        for (int t = 1; uni && t < tb.n_tiles; ++t)
+            uni = tb.tile_elem[t + 1] - tb.tile_elem[t] == te0 && tb.tile_vert[t + 1] - tb.tile_vert[t] == tv0;
+        td.uni_te = uni ? te0 : 0;
+        td.uni_tv = uni ? tv0 : 0;
+    }
     if ((rc = upload(h, tb.tile_elem, &td.tile_elem))) return rc;
     if ((rc = upload(h, tb.tile_vert, &td.tile_vert))) return rc;
     if ((rc = upload(h, tb.lv_gid, &td.lv_gid))) return rc;
@@ -402,6 +410,26 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if ((rc = upload(h, tb.fin_gid, &td.fin_gid))) return rc;
     if ((rc = upload(h, tb.fin_ptr, &td.fin_ptr))) return rc;
     if ((rc = upload(h, tb.vfin, &td.vfin))) return rc;
+    {
+        // packed copies of the vertex tables and of conn + incidence lists,
+        // so that the HVP tile kernel stages a tile with three bulk copies
+        std::vector<int32_t> lv3(tb.lv_gid.size() * 3);
+        for (size_t k = 0; k < tb.lv_gid.size(); ++k) {
+            lv3[3 * k] = tb.lv_gid[k];
+            lv3[3 * k + 1] = tb.lv_code[k];
+            lv3[3 * k + 2] = (int32_t)tb.lv_inc[k];
+        }
+        if ((rc = upload(h, lv3, &td.lv3))) return rc;
+        const size_t per = 4 + 2 * (size_t)nc;
+        std::vector<uint8_t> ci((size_t)tb.ne_int * per);
+        for (int t = 0; t < tb.n_tiles; ++t) {
+            const int64_t es = tb.tile_elem[t], ne_t = tb.tile_elem[t + 1] - es;
+            uint8_t *dst = ci.data() + (size_t)es * per;
+            std::memcpy(dst, tb.conn.data() + es, (size_t)ne_t * 4);
+            std::memcpy(dst + (size_t)ne_t * 4, tb.inc.data() + es * nc, (size_t)ne_t * nc * 2);
+        }
+        if ((rc = upload(h, ci, &td.ci))) return rc;
+    }
     c.threads = h->opt.threads > 0 ? h->opt.threads : (d == 3 ? 128 : 256);
     c.muscle = h->mat.muscle_model;
     if (c.threads % 32 || c.threads > 256) return fail(h, SIM_EINVAL, "threads must be a multiple of 32, at most 256");

@@ -138,15 +138,26 @@ __device__ __forceinline__ void hvp_element(const T *rec, int le, uint32_t cword
 #pragma unroll
         for (int i = 0; i < D; ++i) dvg[i] *= kk * aval;
     }
+    // G = W (dP Dm^-T + dvg g^T), with W folded into the coefficients of dP
+    // and into dvg: dP = mu dF + c'(J) dJ cof F + c(J) dcof(F)[dF] formed once
+    // per row entry, then multiplied by B^T
+    const T muW = mu * W, cpW = cpdJ * W, ccW = cc * W;
+    T M[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        dvg[i] *= W;
+#pragma unroll
+        for (int k = 0; k < D; ++k) M[i][k] = muW * dF[i][k] + cpW * C[i][k] + ccW * dC[i][k];
+    }
     T G[D][D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            T s = T(0);
+            T s = dvg[i] * gv[j];
 #pragma unroll
-            for (int k = 0; k < D; ++k) s += (mu * dF[i][k] + cpdJ * C[i][k] + cc * dC[i][k]) * B[j][k];
-            G[i][j] = W * (s + dvg[i] * gv[j]);
+            for (int k = 0; k < D; ++k) s += M[i][k] * B[j][k];
+            G[i][j] = s;
         }
     if (CG) {
         // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
