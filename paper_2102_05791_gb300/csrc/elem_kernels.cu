@@ -415,13 +415,10 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     // Everything copied so far is static during a solve; state (u, v) and the
     // CG scalars are read only after the predecessor kernel has completed.
     pdl_wait();
-    if (CG && sc->done) {  // CG already finished: drain the copies, then leave
-        if (threadIdx.x == 0) {
-            mbar_wait_bounded(bar, 0);
-            mbar_wait_bounded(bar + 1, 0);
-        }
-        return;
-    }
+    // the flag is read before the wait so that its load overlaps the copies
+    // in flight; the previous kernel has completed, so every thread reads the
+    // same value
+    const int cg_done = CG ? sc->done : 0;
     // every thread takes the same decision, so no thread is left at a barrier
     if (__syncthreads_or(!mbar_wait_bounded(bar, 0, td.wait_polls))) {
         if (threadIdx.x == 0) {
@@ -429,6 +426,10 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
             mbar_wait_bounded(bar, 0);  // give copies in flight a last chance before the CTA exits
             mbar_wait_bounded(bar + 1, 0);
         }
+        return;
+    }
+    if (cg_done) {  // CG already finished: drain the second copy, then leave
+        if (threadIdx.x == 0) mbar_wait_bounded(bar + 1, 0);
         return;
     }
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {

@@ -268,8 +268,9 @@ void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar
 // b = xbar1 + vbar1/dt
 void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out,
                      cudaStream_t s);
-// v1 = (x1 - x0)/dt
+// blocks of the grid-stride vector kernels for n entries
 int vec_grid_size(int64_t n);
+int cg_update_grid_size(int64_t nv);  // blocks of the CG update kernel (one vertex per thread)
 // One block: p.Ap from the HVP tile partials (type T: FP32 partials are summed
 // with compensation) -> sc->alpha, or non-positive curvature.
 template <typename T>
@@ -279,6 +280,7 @@ void launch_residual(const Ctx &c, const double *b, const double *Ax, double *r,
 // x += d
 template <typename T>
 void launch_accumulate(const Ctx &c, double *x, const T *d, cudaStream_t s);
+// v1 = (x1 - x0)/dt
 void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, double *v1,
                      cudaStream_t s);
 

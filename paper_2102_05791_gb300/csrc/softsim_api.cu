@@ -437,7 +437,8 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
 
     // --- work buffers
     const int64_t nd = nv * d;
-    const int n_part = std::max({td.n_tiles + c.n_fin_blocks, vec_grid_size(nd), vec_grid_size(ne_int), 1});
+    const int n_part = std::max({td.n_tiles + c.n_fin_blocks, vec_grid_size(nd), vec_grid_size(ne_int),
+                                  cg_update_grid_size(nv), 1});
     c.partials = (double *)dalloc(h, sizeof(double) * (size_t)n_part * (2 * kMaxTrials + 1));
     h->sc = (DevScalars *)dalloc(h, sizeof(DevScalars));
     c.sc = h->sc;

@@ -11,6 +11,8 @@
 // single term (per thread, over a block, over the blocks' (hi, lo) pairs);
 // p.Ap is summed in plain FP32 within a tile (inside the HVP tile kernel)
 // and with compensation over the tiles.  The double loop sums in FP64.
+#include <algorithm>
+
 #include "internal.h"
 #include "reduce.cuh"
 #include "pdl.cuh"
@@ -24,6 +26,13 @@ static inline int vec_grid(int64_t n)
     if (g > 1216) g = 1216;  // 152 SMs x 8
     return (int)g;
 }
+
+// Grids of the CG loop's vector kernels: every thread takes one vertex
+// (update) or four consecutive entries (direction) and issues all of its
+// loads at once, so each kernel waits on DRAM about once instead of once per
+// grid-stride step.
+static inline int cg_vert_grid(int64_t nv) { return (int)std::max<int64_t>(1, (nv + 255) / 256); }
+static inline int cg_vec4_grid(int64_t n) { return (int)std::max<int64_t>(1, ((n + 3) / 4 + 255) / 256); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double *__restrict__ b, double sign,
@@ -90,12 +99,18 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
                 for (int c = 0; c < D; ++c) d[i * D + c] = p[i * D + c];
             continue;
         }
-        T a[D];
+        // every load of the vertex is issued before any is used (Ap is read at
+        // halo vertices too and ignored there)
         const int f = td.vfin[i];
-        if (f < 0) {
+        T a[D], pv[D], rv[D], dv[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) a[c] = Ap[i * D + c];
-        } else {
+        for (int c = 0; c < D; ++c) {
+            a[c] = Ap[i * D + c];
+            pv[c] = p[i * D + c];
+            rv[c] = r[i * D + c];
+            dv[c] = d[i * D + c];
+        }
+        if (f >= 0) {
             const bool fx = vd.fixed[i] != 0;
 #pragma unroll
             for (int c = 0; c < D; ++c) a[c] = T(0);
@@ -106,13 +121,13 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
                 const double yy = vd.X[i * D + 1] + (double)u[i * D + 1];
                 const double pen = yy < 0.0 ? -yy : 0.0;
                 const double d2 = pen > 0.0 ? ph.cpow * (ph.cpow - 1) * ph.kc * (ph.cpow == 2 ? 1.0 : pen) : 0.0;
-                a[1] += T(ph.s_el * d2) * p[i * D + 1];
+                a[1] += T(ph.s_el * d2) * pv[1];
             }
             if (ph.dyn) {
                 const T m = T(vd.mass[i]);
                 const T mh = ph.fw ? m + T(ph.fw[i]) : m;
 #pragma unroll
-                for (int c = 0; c < D; ++c) a[c] += (c == 1 ? m : mh) * p[i * D + c];
+                for (int c = 0; c < D; ++c) a[c] += (c == 1 ? m : mh) * pv[c];
             }
             if (fx)
 #pragma unroll
@@ -120,8 +135,8 @@ __global__ void __launch_bounds__(256) k_cg_update_halo(TileDev td, VertDev vd, 
         }
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            d[i * D + c] += alpha * p[i * D + c];
-            const T ri = r[i * D + c] - alpha * a[c];
+            d[i * D + c] = dv[c] + alpha * pv[c];
+            const T ri = rv[c] - alpha * a[c];
             r[i * D + c] = ri;
             rr.add(ri * ri);
         }
@@ -181,6 +196,13 @@ __global__ void __launch_bounds__(1024) k_cg_beta(const double *__restrict__ par
     }
 }
 
+// Four entries of a vector in one aligned load or store (the vectors are
+// allocated with 256-byte alignment).
+template <typename T>
+struct alignas(4 * sizeof(T)) Vec4 {
+    T v[4];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, const T *__restrict__ r,
                                                 const DevScalars *sc)
@@ -189,8 +211,17 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, T *__restrict__ p, co
     pdl_wait();  // upstream results are visible past this point
     if (sc->done) return;
     const T beta = pick<T>(sc->beta, sc->beta_f);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = r[i] + beta * p[i];
+    // four consecutive entries per thread and step, both loads issued first
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, n4 = n >> 2;
+    for (int64_t j = q; j < n4; j += (int64_t)gridDim.x * blockDim.x) {
+        Vec4<T> pv = reinterpret_cast<const Vec4<T> *>(p)[j];
+        const Vec4<T> rv = reinterpret_cast<const Vec4<T> *>(r)[j];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv.v[k] = rv.v[k] + beta * pv.v[k];
+        reinterpret_cast<Vec4<T> *>(p)[j] = pv;
+    }
+    const int64_t t = (n4 << 2) + q;  // the last n mod 4 entries
+    if (t < n) p[t] = r[t] + beta * p[t];
 }
 
 template <typename T>
@@ -401,7 +432,7 @@ void launch_cg_update_halo(const Ctx &c, const Phys &ph, const T *u, T *d, T *r,
                            const T *hp, cudaStream_t s)
 {
     c.n_launch += 2;
-    const int g = vec_grid(c.nv * 4);
+    const int g = cg_vert_grid(c.nv);
     if (c.dim == 2)
         launch_k(c.pdl, k_cg_update_halo<T, 2>, dim3(g), dim3(256), 0, s, c.td, c.vd, ph, u, d, r, p, Ap, hp,
                  c.partials, c.sc);
@@ -423,7 +454,7 @@ void launch_cg_dir(const Ctx &c, T *p, const T *r, cudaStream_t s)
 {
     c.n_launch += 1;
     const int64_t n = c.nv * c.dim;
-    launch_k(c.pdl, k_cg_dir<T>, dim3(vec_grid(n)), dim3(256), 0, s, n, p, (const T *)r, (const DevScalars *)c.sc);
+    launch_k(c.pdl, k_cg_dir<T>, dim3(cg_vec4_grid(n)), dim3(256), 0, s, n, p, (const T *)r, (const DevScalars *)c.sc);
 }
 
 template <typename T>
@@ -516,6 +547,7 @@ void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, d
 }
 
 int vec_grid_size(int64_t n) { return vec_grid(n); }
+int cg_update_grid_size(int64_t nv) { return cg_vert_grid(nv); }
 
 #define INST(T)                                                                                                     \
     template void launch_cg_init<T>(const Ctx &, const double *, double, T *, T *, T *, double, int, int,            \
