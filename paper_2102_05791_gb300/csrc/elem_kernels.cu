@@ -435,11 +435,18 @@ __global__ void __launch_bounds__(256, MINB) k_tile_hvp(TileDev td, const T *__r
     for (int k = threadIdx.x; k < nlv; k += blockDim.x) {
         const int64_t gid = sLv[3 * k];
         const bool fx = ((uint32_t)sLv[3 * k + 2] & kLvPinned) != 0;
+        if constexpr (CG && sizeof(T) == 4 && D == 3) {
+            // the CG loop's 3D FP32 displacement comes in 16-byte rows
+            const float4 u4 = reinterpret_cast<const float4 *>(u)[gid];
+            suv[k * 6 + 0] = u4.x;
+            suv[k * 6 + 1] = u4.y;
+            suv[k * 6 + 2] = u4.z;
+        } else {
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            suv[k * 2 * D + c] = u[gid * D + c];
-            suv[k * 2 * D + D + c] = fx ? T(0) : v[gid * D + c];
+            for (int c = 0; c < D; ++c) suv[k * 2 * D + c] = u[gid * D + c];
         }
+#pragma unroll
+        for (int c = 0; c < D; ++c) suv[k * 2 * D + D + c] = fx ? T(0) : v[gid * D + c];
     }
     if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) {
         if (threadIdx.x == 0) {

@@ -268,6 +268,8 @@ void launch_step_bwd_combine(const Ctx &c, const double *lam, const double *vbar
 // b = xbar1 + vbar1/dt
 void launch_axpy_out(int64_t n, const double *x, const double *y, double beta, double *out,
                      cudaStream_t s);
+// u4[i] = (u[3i], u[3i+1], u[3i+2], 0) for the 3D FP32 CG tile kernel
+void launch_pad_rows4(const Ctx &c, const float *u, float *u4, cudaStream_t s);
 // blocks of the grid-stride vector kernels for n entries
 int vec_grid_size(int64_t n);
 int cg_update_grid_size(int64_t nv);  // blocks of the CG update kernel (one vertex per thread)

@@ -55,6 +55,7 @@ struct sim_handle {
     double *u = nullptr, *uhat = nullptr, *g = nullptr, *hp64 = nullptr, *a64 = nullptr;
     double *fw = nullptr, *u0 = nullptr;  // ground friction of the current step (null when off)
     float *u32 = nullptr, *hp32 = nullptr;
+    float *u4 = nullptr;  // 3D FP32 displacement in 16-byte rows, as the CG tile kernel gathers it
     void *vd = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr;  // CG vectors in the HVP precision
     double *work = nullptr, *lam = nullptr, *lacc = nullptr, *r64 = nullptr, *Hx = nullptr;
     int verbose = 0;
@@ -460,6 +461,10 @@ static int create_impl(sim_handle *h, const sim_mesh *mesh, const sim_material *
     if (is_mixed(h)) {
         h->u32 = (float *)dalloc(h, sizeof(float) * nd);
         h->hp32 = (float *)dalloc(h, sizeof(float) * std::max<int64_t>(tb.n_slots, 1) * d);
+        if (d == 3) {
+            h->u4 = (float *)dalloc(h, sizeof(float) * 4 * nv);
+            if (!h->u4) return fail(h, SIM_ENOMEM, "device allocation failed");
+        }
     }
     if (!c.partials || !h->sc || !h->u || !h->uhat || !h->g || !h->work || !h->lam || !h->lacc || !h->r64 || !h->Hx || !h->hp64 || !h->a64 || !h->vd ||
         !h->vr || !h->vp || !h->vAp || (is_mixed(h) && (!h->u32 || !h->hp32)))
@@ -530,11 +535,14 @@ struct View;
 template <>
 struct View<float> {
     static float *u(sim_handle *h) { return h->u32; }
+    // the displacement as the CG tile kernel reads it (refresh_cg_u first)
+    static const float *ucg(sim_handle *h) { return h->u4 ? h->u4 : h->u32; }
     static float *hp(sim_handle *h) { return h->hp32; }
 };
 template <>
 struct View<double> {
     static double *u(sim_handle *h) { return h->u; }
+    static const double *ucg(sim_handle *h) { return h->u; }
     static double *hp(sim_handle *h) { return h->hp64; }
 };
 
@@ -560,6 +568,14 @@ static int set_state(sim_handle *h, const double *x, bool pin, cudaStream_t s)
 
 // ---------------------------------------------------------------- CG
 
+// Copies the FP32 displacement into the padded rows the 3D CG tile kernel
+// gathers (one 16-byte load per vertex); the displacement is constant during
+// a CG solve.
+static void refresh_cg_u(sim_handle *h, cudaStream_t s)
+{
+    if (h->u4) launch_pad_rows4(h->ctx, h->u32, h->u4, s);
+}
+
 template <typename T>
 static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s, int n_iter = kCgBlock, bool pdl = true)
 {
@@ -568,7 +584,7 @@ static void enqueue_cg_block(sim_handle *h, const Phys &ph, cudaStream_t s, int 
     for (int k = 0; k < n_iter; ++k) {
         // the timing events bracket the HVP tile kernel alone
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k], s, cudaEventRecordExternal);
-        launch_hvp_cg<T>(h->ctx, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
+        launch_hvp_cg<T>(h->ctx, ph, View<T>::ucg(h), p, Ap, View<T>::hp(h), s);
         if (h->timing) cudaEventRecordWithFlags(h->tev[2 * k + 1], s, cudaEventRecordExternal);
         launch_cg_alpha<T>(h->ctx, h->ctx.td.n_tiles, s);
         launch_cg_update_halo<T>(h->ctx, ph, View<T>::u(h), d, r, p, Ap, View<T>::hp(h), s);
@@ -675,6 +691,7 @@ static int run_cg(sim_handle *h, const Phys &ph, int max_iter, cudaStream_t s)
                                 View<T>::hp(h), s));
         return read_scalars(h, s);
     }
+    refresh_cg_u(h, s);
     if (!h->timing) {
         cudaGraphExec_t wexec = get_cg_while<T>(h, ph);
         if (wexec) {
@@ -952,7 +969,8 @@ static int hvp_dot_impl(sim_handle *h, const void *v, void *Hv, double *vHv, cud
     T *p = (T *)h->vp, *Ap = (T *)h->vAp;
     CK(h, cudaMemcpyAsync(p, v, sizeof(T) * nd, cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemsetAsync(&h->sc->done, 0, sizeof(int), s));  // the CG tile kernel skips its work once CG is done
-    launch_hvp_cg<T>(c, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
+    refresh_cg_u(h, s);
+    launch_hvp_cg<T>(c, ph, View<T>::ucg(h), p, Ap, View<T>::hp(h), s);
     launch_hvp_finalize_only<T>(c, ph, View<T>::u(h), p, Ap, View<T>::hp(h), s);
     launch_tile_dot<T>(c, &h->sc->pAp, s);
     CKL(h);

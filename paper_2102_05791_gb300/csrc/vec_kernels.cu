@@ -546,6 +546,18 @@ void launch_velocity(int64_t n, const double *x1, const double *x0, double dt, d
     k_velocity<<<vec_grid(n), 256, 0, s>>>(n, x1, x0, dt, v1);
 }
 
+__global__ void k_pad_rows4(int64_t nv, const float *__restrict__ u, float4 *__restrict__ u4)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        u4[i] = make_float4(u[3 * i], u[3 * i + 1], u[3 * i + 2], 0.0f);
+}
+
+void launch_pad_rows4(const Ctx &c, const float *u, float *u4, cudaStream_t s)
+{
+    c.n_launch += 1;
+    k_pad_rows4<<<vec_grid(c.nv), 256, 0, s>>>(c.nv, u, reinterpret_cast<float4 *>(u4));
+}
+
 int vec_grid_size(int64_t n) { return vec_grid(n); }
 int cg_update_grid_size(int64_t nv) { return cg_vert_grid(nv); }
 
