@@ -230,11 +230,15 @@ def run_dynamics(dev):
     a_groups = torch.from_numpy(p.extra["a_groups"]).to(dev)
     x0 = torch.from_numpy(p.X).to(dev)
     a_seq = a_groups[:, group].contiguous()
-    # untimed warm-up on the same handle: CUDA-graph capture and module loading
+    # untimed warm-up on the same handle: CUDA-graph capture and module loading,
+    # including the group sum (the first index_add_ of a process can spend
+    # seconds loading and JIT-compiling PyTorch's kernel for this GPU)
     _, _, ckw, _ = sim.rollout(x0, torch.zeros_like(x0), a_seq[:20].contiguous(), ckpt_every=20)
-    sim.rollout_backward(a_seq[:20].contiguous(), ckw, 20, torch.zeros_like(x0), torch.zeros_like(x0))
+    _, _, abw, _ = sim.rollout_backward(a_seq[:20].contiguous(), ckw, 20, torch.zeros_like(x0), torch.zeros_like(x0))
+    torch.zeros_like(a_groups[:20]).index_add_(1, group, abw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    n_launch0 = sim.kernel_launches()
     xT, vT, ck, st = sim.rollout(x0, torch.zeros_like(x0), a_seq, ckpt_every=20)
     xbT = torch.zeros_like(x0)
     xbT[:, 0] = 1.0 / p.n_vert
@@ -242,12 +246,14 @@ def run_dynamics(dev):
     g = torch.zeros_like(a_groups).index_add_(1, group, ab)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    n_launch = sim.kernel_launches() - n_launch0
     sim.close()
     res = {"workload": "64x32 grid (4,096 tris), 200 backward-Euler steps, checkpoints every 20, forward + BPTT "
                        "(after an untimed 20-step warm-up)", "tile_shape": list(sim.tile_shape),
            "adjoint_rtol": 1e-8, "seconds": dt, "steps_per_s": 200 * 2 / dt,
            "newton_iters": st["newton_iters"] + stb["newton_iters"],
-           "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm())}
+           "cg_iters": st["cg_iters_total"] + stb["cg_iters_total"], "grad_norm": float(g.norm()),
+           "gpu_launches": int(n_launch)}
     acc = None
     gpath = os.path.join(GOLDEN, "c2_bptt_oracle.npz")
     if os.path.exists(gpath):
