@@ -16,8 +16,10 @@ Printed JSON line (rank 0):
   roofline   the HVP tile kernel: algorithmic bytes per launch (72 B per tet +
              36 B per vertex) / its mean duration, against the HBM peak;
   accuracy   the GPU results against the FP64 oracle's own stored solutions
-             (tests/golden): the large body at 1/8 size in both precisions,
-             three bodies of the batch, the 200-step walker's BPTT gradient;
+             (tests/golden): the large body at 1/8 size and the config-3 box
+             in both precisions, three bodies of the batch, the 200-step
+             walker's BPTT gradient, and the mixed CG inner product against
+             FP64;
   cpu_baseline  the FP64 oracle on the host cores: element-HVP/s and
              gradient evaluations/s on the large body (one core and all
              cores, one process per core on element slices), and solve wall
@@ -266,20 +268,23 @@ def run_dynamics(dev):
     return res, acc
 
 
-def run_accuracy_eighth(dev):
-    """The large body at 1/8 size (393,216 tets): forward solve, adjoint and
+def run_accuracy_quasistatic(dev, name):
+    """A quasistatic workload (the large body at 1/8 size, 393,216 tets, or the
+    2 x 1 x 1 box of config 3, 40,960 tets): forward solve, adjoint and
     parameter VJP on the GPU in both precisions, against the oracle's stored
     x*, lambda and dL/da (Newton to 1e-10, adjoint to 1e-11)."""
     import torch
     import synth
     from paper_2102_05791_gb300 import api
-    gpath = os.path.join(GOLDEN, "c5_eighth_oracle.npz")
+    gpath = os.path.join(GOLDEN, f"{name}_oracle.npz")
     if not os.path.exists(gpath):
         return None
     g = np.load(gpath)
-    p = synth.make_config5(2)
-    out = {"against": "oracle solution stored in tests/golden/c5_eighth_oracle.npz", "workload":
-           "box 4x2x2, 64x32x32 hex x 6 tets (393,216 tets, 70,785 vertices)"}
+    if name == "c5_eighth":
+        p, desc = synth.make_config5(2), "box 4x2x2, 64x32x32 hex x 6 tets (393,216 tets, 70,785 vertices)"
+    else:
+        p, desc = synth.make_config3(), "box 2x1x1, 32x16x16 hex x 5 tets (40,960 tets, 9,537 vertices)"
+    out = {"against": f"oracle solution stored in tests/golden/{name}_oracle.npz", "workload": desc}
     for prec, kw in (("mixed", {"tile_elems": "auto"}), ("fp64", {"adjoint_rtol": 1e-10})):
         sim = api.Simulator(p.X, p.T, p.fixed, p.fiber, mu=p.mu, lam=p.lam, k_muscle=p.k_muscle,
                             density=p.density, gravity=p.gravity, precision=prec, device=dev, **kw)
@@ -731,7 +736,8 @@ def run_ours(args, rank, world, local_rank):
         xs_last = sim.solve(a)[0]
         accuracy["cg_dot"] = run_dot_accuracy(sim, sim64, xs_last, a, dev)
         sim64.close()
-        accuracy["large_body_eighth"] = run_accuracy_eighth(dev)
+        accuracy["large_body_eighth"] = run_accuracy_quasistatic(dev, "c5_eighth")
+        accuracy["box_c3"] = run_accuracy_quasistatic(dev, "c3")
     if not args.no_batched:
         line["batched"], accuracy["batched_bodies"] = run_batched(dev, max(1, min(args.steps, 3)), 1,
                                                                   args.plain_strata)

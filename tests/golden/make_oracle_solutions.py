@@ -11,6 +11,9 @@ the benchmark's accuracy report compare the GPU results with these files.
   oracle's Newton-CG to |grad E| <= 1e-10 |grad E_0|, the adjoint
   lambda = H^-1 dL/dx (Eq. dLda-re-ordered) by CG to 1e-11 relative residual,
   and dL/da = -lambda^T d2E/dx da, for L = 1/2 |mean(x) - target|^2.
+* ``c3_oracle.npz`` -- the 2 x 1 x 1 box (32 x 16 x 16 hexes x 5 tets: 9,537
+  vertices, 40,960 tets; seed 20210211 + 3), the same three quantities as for
+  the large body, at the same tolerances.
 * ``c2_bptt_oracle.npz`` -- the 64 x 32 walker (2,145 vertices, 4,096 tris;
   seed 20210211 + 2), 200 backward-Euler steps (Eq. opt-be) at rtol 1e-10,
   then backpropagation through time (Sec. 4) of the horizontal displacement
@@ -50,6 +53,29 @@ C4_PICK_QUANTILES = (0.0, 0.5, 0.8)   # positions in the batch sorted by triangl
 def c4_pick(probs):
     order = np.argsort([p.n_elem for p in probs], kind="stable")
     return [int(order[int(q * len(order))]) if q < 1.0 else int(order[-1]) for q in C4_PICK_QUANTILES]
+
+
+def _quasistatic(p, name, seed):
+    import oracle
+    m = oracle.make_model(p)
+    t0 = time.perf_counter()
+    x, st = m.newton(p.a, rtol=C5_NEWTON_RTOL)
+    if st["status"] != oracle.OK:
+        raise RuntimeError(f"oracle Newton status {st}")
+    gL = oracle.mean_loss_grad(x, p.target)
+    lam, it = m.adjoint(x, p.a, gL, rtol=C5_ADJ_RTOL)
+    dLda = m.param_vjp(x, lam, p.a)
+    wall = time.perf_counter() - t0
+    np.savez_compressed(os.path.join(HERE, name), u_star=x - p.X, lam=lam, dLda=dLda,
+                        newton_rtol=C5_NEWTON_RTOL, adjoint_rtol=C5_ADJ_RTOL, seed=seed,
+                        newton_iters=st["newton_iters"], cg_iters=st["cg_iters_total"], adjoint_cg_iters=it,
+                        res0=st["res0"], res_final=st["res_final"], wall_s=wall)
+    return f"{name}: newton {st['newton_iters']} cg {st['cg_iters_total']} adjoint cg {it}, {wall:.0f} s"
+
+
+def c3():
+    import synth
+    return _quasistatic(synth.make_config3(), "c3_oracle.npz", synth.BASE_SEED + 3)
 
 
 def c5_eighth():
@@ -120,11 +146,11 @@ def c4_bodies():
 
 
 def _run(name):
-    return {"c5_eighth": c5_eighth, "c2_bptt": c2_bptt, "c4_bodies": c4_bodies}[name]()
+    return {"c5_eighth": c5_eighth, "c3": c3, "c2_bptt": c2_bptt, "c4_bodies": c4_bodies}[name]()
 
 
 def main(argv):
-    names = argv or ["c5_eighth", "c2_bptt", "c4_bodies"]
+    names = argv or ["c5_eighth", "c3", "c2_bptt", "c4_bodies"]
     import oracle
     oracle.build()
     with mp.get_context("spawn").Pool(len(names)) as pool:

@@ -1,7 +1,7 @@
 """The stored oracle solutions (tests/golden/*_oracle.npz) against the oracle's
 own definitions, on the CPU.
 
-The large 3D body at 1/8 size: the stored state satisfies the Newton
+The large 3D body at 1/8 size and the 2 x 1 x 1 box of config 3: the stored state satisfies the Newton
 tolerance it was solved to (|grad E(x*)| <= 1e-10 |grad E(X)|, Eq.
 x1-quasistatic-argmin), the stored lambda solves H lambda = dL/dx to within
 ten times the adjoint CG tolerance (CG stops on its recurred residual), and
@@ -19,10 +19,11 @@ import synth
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def test_large_body_eighth_solution_is_the_oracles():
-    g = np.load(os.path.join(GOLDEN, "c5_eighth_oracle.npz"))
-    p = synth.make_config5(2)
-    assert int(g["seed"]) == synth.BASE_SEED + 5
+@pytest.mark.parametrize("name", ["c5_eighth", "c3"])
+def test_quasistatic_solution_is_the_oracles(name):
+    g = np.load(os.path.join(GOLDEN, f"{name}_oracle.npz"))
+    p = synth.make_config5(2) if name == "c5_eighth" else synth.make_config3()
+    assert int(g["seed"]) == synth.BASE_SEED + (5 if name == "c5_eighth" else 3)
     m = oracle.make_model(p)
     x = p.X + g["u_star"]
     g0 = np.linalg.norm(m.grad(p.X, p.a))
@@ -55,7 +56,8 @@ def test_dynamics_solutions_have_the_workload_shapes():
         assert np.isfinite(c4[f"abar_{k}"]).all()
 
 
-@pytest.mark.parametrize("name", ["c5_eighth_oracle.npz", "c2_bptt_oracle.npz", "c4_bodies_oracle.npz"])
+@pytest.mark.parametrize("name", ["c5_eighth_oracle.npz", "c3_oracle.npz", "c2_bptt_oracle.npz",
+                                  "c4_bodies_oracle.npz"])
 def test_solution_files_record_their_tolerances(name):
     g = np.load(os.path.join(GOLDEN, name))
     assert "wall_s" in g and float(g["wall_s"]) > 0.0

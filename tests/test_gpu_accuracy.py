@@ -3,11 +3,12 @@
 The stored solutions (tests/golden/*_oracle.npz) are written by
 tests/golden/make_oracle_solutions.py, which calls only the FP64 oracle:
 
-* the large 3D body at 1/8 size (64 x 32 x 32 hexes x 6 tets, 393,216 tets):
-  the quasistatic state x* (Eq. x1-quasistatic-argmin), the adjoint lambda and
-  dL/da (Eq. dLda-re-ordered) of L = 1/2 |mean(x) - target|^2, compared with
-  the GPU's forward solve, adjoint and parameter VJP in both precisions, in
-  the benchmark's launch configuration (autotuned tiles for the mixed path);
+* the large 3D body at 1/8 size (64 x 32 x 32 hexes x 6 tets, 393,216 tets)
+  and the 2 x 1 x 1 box of config 3 (40,960 tets): the quasistatic state x*
+  (Eq. x1-quasistatic-argmin), the adjoint lambda and dL/da (Eq.
+  dLda-re-ordered) of L = 1/2 |mean(x) - target|^2, compared with the GPU's
+  forward solve, adjoint and parameter VJP in both precisions, in the
+  benchmark's launch configuration (autotuned tiles for the mixed path);
 * the 64 x 32 walker, 200 backward-Euler steps (Eq. opt-be) with BPTT
   (Sec. 4): the final state and dL/d(a_groups), against the checkpointed GPU
   rollout and its backward as the benchmark runs them (adjoints to 1e-8: at
@@ -38,9 +39,10 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_large_body_eighth_matches_oracle_solution(precision):
-    g = np.load(os.path.join(GOLDEN, "c5_eighth_oracle.npz"))
-    p = synth.make_config5(2)
+@pytest.mark.parametrize("name", ["c5_eighth", "c3"])
+def test_quasistatic_workload_matches_oracle_solution(name, precision):
+    g = np.load(os.path.join(GOLDEN, f"{name}_oracle.npz"))
+    p = synth.make_config5(2) if name == "c5_eighth" else synth.make_config3()
     kw = {"tile_elems": "auto"} if precision == "mixed" else {"adjoint_rtol": 1e-10}
     sim = make_sim(p, precision, **kw)
     a = dev(p.a)
