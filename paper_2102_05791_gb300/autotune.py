@@ -23,8 +23,10 @@ import numpy as np
 
 CANDIDATES = {
     3: [(384, 128), (384, 256), (256, 128), (512, 128), (512, 256), (768, 256)],
-    # small tiles give small meshes more CTAs (a 4,096-triangle body has only 8 tiles of 512)
-    2: [(512, 256), (512, 128), (384, 128), (768, 256), (1024, 256), (128, 128), (64, 64)],
+    # small tiles give small meshes more CTAs (a 4,096-triangle body has only 8 tiles of 512);
+    # at most 16 tiles run the CG solve as one thread-block cluster
+    2: [(512, 256), (512, 128), (384, 128), (768, 256), (1024, 256), (256, 256), (256, 128), (128, 128),
+        (64, 64)],
 }
 
 

@@ -1,6 +1,8 @@
-// Grid-wide barrier for cooperative launches (all CTAs co-resident).
+// Grid-wide barrier for cooperative launches (all CTAs co-resident), and the
+// cluster barrier and distributed-shared-memory loads for one-cluster grids.
 #pragma once
 
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace softsim {
@@ -37,6 +39,46 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *word, unsigned int n_
     }
     __syncthreads();
     return ok_s != 0;
+}
+
+// Thread-block cluster primitives (the whole grid is one cluster of at most
+// 16 CTAs): a hardware barrier over every thread of the cluster with
+// release/acquire semantics at cluster scope, and loads from another CTA's
+// shared memory (distributed shared memory).
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of the same shared-memory object in the CTA of the given cluster rank.
+__device__ __forceinline__ uint32_t dsmem_addr(const void *local, uint32_t rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float2 ld_dsmem_f2(const void *local, uint32_t rank)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(dsmem_addr(local, rank))
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ double ld_dsmem_f64(const void *local, uint32_t rank)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_dsmem_s32(const void *local, uint32_t rank)
+{
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
 }
 
 }  // namespace softsim

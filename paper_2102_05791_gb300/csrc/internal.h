@@ -169,7 +169,9 @@ struct Ctx {
     DevScalars *sc = nullptr;
     mutable int64_t n_launch = 0;  // kernels launched through this context
     mutable bool pdl = false;      // launch CG-loop kernels with programmatic dependent launch
-    mutable int coop_fit[2] = {-1, -1};  // [FP32, FP64] cooperative CG kernel fits: 1 / 0, -1 = not checked
+    // [FP32, FP64] the cooperative CG kernel fits as a cooperative grid, then
+    // [FP32, FP64] as one thread-block cluster: 1 / 0, -1 = not checked
+    mutable int coop_fit[4] = {-1, -1, -1, -1};
 };
 
 // ---------------------------------------------------------------- launchers
