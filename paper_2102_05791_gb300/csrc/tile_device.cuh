@@ -95,9 +95,59 @@ __device__ __forceinline__ void hvp_element(const T *rec, int le, uint32_t cword
 #pragma unroll
     for (int i = 0; i < D; ++i) gv[i] = rv[FI<D>::G + i];
     const T W = rv[FI<D>::W] * sel;
-    edges_uv<T, D>(suv, lid, Du, Dv);
-    mul<T, D>(Du, B, F, true);
-    mul<T, D>(Dv, B, dF, false);
+    if constexpr (sizeof(T) == 4 && D == 3) {
+        // paired FP32 arithmetic (__fadd2_rn / __ffma2_rn: two lanes per
+        // instruction), the same operations in the same order as the scalar
+        // form below, so the results are bitwise the same: a staged vertex is
+        // the pairs (u0, u1), (u2, v0), (v1, v2), so the edges come as pairs
+        // (Du0k, Du1k), (Du2k, Dv0k), (Dv1k, Dv2k), and F = I + Du B and
+        // dF = Dv B as pairs (F0j, F1j), (F2j, dF0j), (dF1j, dF2j) with B[k][j]
+        // on both lanes (27 paired FMAs instead of 54)
+        const float2 *sp = reinterpret_cast<const float2 *>(suv);
+        const float2 a0 = sp[3 * lid[0]], b0 = sp[3 * lid[0] + 1], c0 = sp[3 * lid[0] + 2];
+        const float2 na0 = make_float2(-a0.x, -a0.y), nb0 = make_float2(-b0.x, -b0.y),
+                     nc0 = make_float2(-c0.x, -c0.y);
+        float2 P1[3], P2[3], P3[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int q = 3 * lid[k + 1];
+            P1[k] = __fadd2_rn(sp[q], na0);
+            P2[k] = __fadd2_rn(sp[q + 1], nb0);
+            P3[k] = __fadd2_rn(sp[q + 2], nc0);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float2 x = make_float2(j == 0 ? 1.0f : 0.0f, j == 1 ? 1.0f : 0.0f);
+            float2 y = make_float2(j == 2 ? 1.0f : 0.0f, 0.0f);
+            float2 z = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float2 bb = make_float2(B[k][j], B[k][j]);
+                x = __ffma2_rn(P1[k], bb, x);
+                y = __ffma2_rn(P2[k], bb, y);
+                z = __ffma2_rn(P3[k], bb, z);
+            }
+            F[0][j] = x.x;
+            F[1][j] = x.y;
+            F[2][j] = y.x;
+            dF[0][j] = y.y;
+            dF[1][j] = z.x;
+            dF[2][j] = z.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Du[0][k] = P1[k].x;
+            Du[1][k] = P1[k].y;
+            Du[2][k] = P2[k].x;
+            Dv[0][k] = P2[k].y;
+            Dv[1][k] = P3[k].x;
+            Dv[2][k] = P3[k].y;
+        }
+    } else {
+        edges_uv<T, D>(suv, lid, Du, Dv);
+        mul<T, D>(Du, B, F, true);
+        mul<T, D>(Dv, B, dF, false);
+    }
     cof<T, D>(F, C);
     dcof<T, D>(F, dF, dC);
     const T J = detF<T, D>(F, C);
