@@ -708,7 +708,9 @@ size_t hvp_smem(const Ctx &c)
 // Resident CTAs per SM that the tile's shared memory allows (at most 4);
 // the kernel variant compiled for that count caps registers to match.  (At
 // 128 threads and 7 resident tiles, the 64-register FP32 variant measured
-// faster in-solve than the 72-register one: 66.3 vs 68.4 us on the large body.)
+// faster in-solve than the 72-register one before the element used paired
+// FP32 arithmetic: 66.3 vs 68.4 us on the large body; with it, the CG variant
+// spills at 64 and runs at 58.4 us with 72 against 60.7 us.)
 template <typename T>
 int hvp_blocks_per_sm(const Ctx &c)
 {
@@ -744,7 +746,10 @@ static void hvp_tile(const Ctx &c, const Phys &ph, const T *u, const T *v, T *y,
         if (c.dim == 2)
             (b >= 4 ? hvp_tile_v<T, 2, CG, 4> : hvp_tile_v<T, 2, CG, 3>)(c, ph, u, v, y, hp, s);
         else
-            (b >= 4 ? hvp_tile_v<T, 3, CG, 4> : hvp_tile_v<T, 3, CG, 3>)(c, ph, u, v, y, hp, s);
+            // the CG variant also forms p.Ap: at 64 registers it spilled, at
+            // the 3-CTA bound it takes 72, which still lets 7 of the
+            // 128-thread tiles be resident (shared memory allows 7)
+            ((b >= 4 && !CG) ? hvp_tile_v<T, 3, CG, 4> : hvp_tile_v<T, 3, CG, 3>)(c, ph, u, v, y, hp, s);
     } else {
         if (c.dim == 2)
             (b >= 2 ? hvp_tile_v<T, 2, CG, 2> : hvp_tile_v<T, 2, CG, 1>)(c, ph, u, v, y, hp, s);

@@ -98,7 +98,7 @@ __device__ __forceinline__ void hvp_element(const T *rec, int le, uint32_t cword
     if constexpr (sizeof(T) == 4 && D == 3) {
         // paired FP32 arithmetic (__fadd2_rn / __ffma2_rn: two lanes per
         // instruction), the same operations in the same order as the scalar
-        // form below, so the results are bitwise the same: a staged vertex is
+        // form below, so this step's results are bitwise the same: a staged vertex is
         // the pairs (u0, u1), (u2, v0), (v1, v2), so the edges come as pairs
         // (Du0k, Du1k), (Du2k, Dv0k), (Dv1k, Dv2k), and F = I + Du B and
         // dF = Dv B as pairs (F0j, F1j), (F2j, dF0j), (dF1j, dF2j) with B[k][j]
@@ -193,23 +193,59 @@ __device__ __forceinline__ void hvp_element(const T *rec, int le, uint32_t cword
     // per row entry, then multiplied by B^T
     const T muW = mu * W, cpW = cpdJ * W, ccW = cc * W;
     T M[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        dvg[i] *= W;
-#pragma unroll
-        for (int k = 0; k < D; ++k) M[i][k] = muW * dF[i][k] + cpW * C[i][k] + ccW * dC[i][k];
-    }
     T G[D][D];
+    if constexpr (sizeof(T) == 4 && D == 3) {
+        // rows 1 and 2 of M and G as pairs (dF rows 1 and 2 already are one),
+        // row 0 scalar, in one fixed FMA order; p.Ap accumulated column by
+        // column as G is formed, so each Dv entry dies once used
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+        for (int i = 0; i < D; ++i) dvg[i] *= W;
+        const float2 muW2 = make_float2(muW, muW), cpW2 = make_float2(cpW, cpW), ccW2 = make_float2(ccW, ccW);
+        float2 m12[3];
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T s = dvg[i] * gv[j];
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += M[i][k] * B[j][k];
-            G[i][j] = s;
+        for (int k = 0; k < 3; ++k) {
+            M[0][k] = fmaf(ccW, dC[0][k], fmaf(cpW, C[0][k], muW * dF[0][k]));
+            m12[k] = __ffma2_rn(ccW2, make_float2(dC[1][k], dC[2][k]),
+                                __ffma2_rn(cpW2, make_float2(C[1][k], C[2][k]),
+                                           __fmul2_rn(muW2, make_float2(dF[1][k], dF[2][k]))));
         }
-    if (CG) {
+        const float2 dv12 = make_float2(dvg[1], dvg[2]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float s = dvg[0] * gv[j];
+            float2 s12 = __fmul2_rn(dv12, make_float2(gv[j], gv[j]));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s = fmaf(M[0][k], B[j][k], s);
+                s12 = __ffma2_rn(m12[k], make_float2(B[j][k], B[j][k]), s12);
+            }
+            G[0][j] = s;
+            G[1][j] = s12.x;
+            G[2][j] = s12.y;
+            if (CG) {  // v_e . (H_e v_e) = Dv : G, column by column
+                qsum += Dv[0][j] * G[0][j];
+                qsum += Dv[1][j] * G[1][j];
+                qsum += Dv[2][j] * G[2][j];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            dvg[i] *= W;
+#pragma unroll
+            for (int k = 0; k < D; ++k) M[i][k] = muW * dF[i][k] + cpW * C[i][k] + ccW * dC[i][k];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                T s = dvg[i] * gv[j];
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += M[i][k] * B[j][k];
+                G[i][j] = s;
+            }
+    }
+    if (CG && !(sizeof(T) == 4 && D == 3)) {
         // sum over corners of v_k . f_k = sum_j Dv[:,j] . G[:,j]
 #pragma unroll
         for (int i = 0; i < D; ++i)
