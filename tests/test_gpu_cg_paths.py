@@ -1,9 +1,12 @@
 """The two ways the library runs a CG solve agree.
 
 SIM_CG_AUTO runs a whole CG solve of a mesh whose tiles fit on the GPU at
-once as one cooperative kernel (tile data staged in shared memory once, three
-grid barriers per iteration); SIM_CG_ITERATION launches the HVP tile kernel
-and the small vector kernels per iteration.  Both solve the same systems with
+once as one kernel (tile data staged in shared memory once, two barriers per
+iteration): as one thread-block cluster when the mesh has at most 16 tiles
+(the small meshes here: cluster barrier, partial sums read from the other
+CTAs' shared memory), else as a cooperative grid (the walker mesh in 32
+tiles: L2 atomic barrier); SIM_CG_ITERATION launches the HVP tile kernel and
+the small vector kernels per iteration.  Both solve the same systems with
 different summation orders, so quasistatic solves, adjoints and a
 backward-Euler step with its backward must agree within the parity
 tolerances, and the cooperative path must launch far fewer kernels.
