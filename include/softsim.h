@@ -118,9 +118,10 @@ typedef struct {
     int max_ls;               /* backtracking halvings cap */
     int tile_elems;           /* elements per tile (0 = library default) */
     int threads;              /* threads per element-kernel block (0 = default) */
-    int cg_kernel;            /* SIM_CG_AUTO: a whole CG solve in one cooperative
-                                 kernel when every tile of the mesh fits on the GPU
-                                 at once, else per-iteration kernels;
+    int cg_kernel;            /* SIM_CG_AUTO: a whole CG solve in one kernel when
+                                 every tile of the mesh fits on the GPU at once (one
+                                 thread-block cluster for at most 16 tiles, else a
+                                 cooperative grid), else per-iteration kernels;
                                  SIM_CG_ITERATION: always per-iteration kernels */
 } sim_options;
 
